@@ -1,0 +1,72 @@
+"""Dense-matrix restatements used to pin the oracle (exact diagonalisation).
+
+Written independently of ``oracle/``: these build H, V and [X,H] as dense numpy
+matrices from the paper's input form and evaluate the paper's quantities by
+eigendecomposition (numpy.linalg.eigh), which is exact up to rounding.
+"""
+import numpy as np
+
+
+def dense_h(lat, scale=1.0):
+    """Dense H / scale (Eq. 32): H[i, nb] += hop, H[i, i] = U_i."""
+    n = lat.n
+    H = np.zeros((n, n), np.complex128)
+    for i in range(n):
+        H[i, i] += lat.onsite[i]
+        for k in range(lat.nb_count[i]):
+            H[i, lat.nb_idx[i, k]] += lat.hop[i, k]
+    return H / scale
+
+
+def dense_xh(lat, scale=1.0):
+    """Dense [X, H]/scale with [X,H]_mn = (X_m - X_n) H_mn = -dx_mn H_mn."""
+    n = lat.n
+    D = np.zeros((n, n), np.complex128)
+    for i in range(n):
+        for k in range(lat.nb_count[i]):
+            D[i, lat.nb_idx[i, k]] += -lat.dx[i, k] * lat.hop[i, k]
+    return D / scale
+
+
+def dense_v(lat):
+    """V = i [H, X] (Eq. 34), i.e. V_mn = i (X_n - X_m) H_mn."""
+    return 1j * _dxh(lat)
+
+
+def _dxh(lat):
+    n = lat.n
+    D = np.zeros((n, n), np.complex128)
+    for i in range(n):
+        for k in range(lat.nb_count[i]):
+            D[i, lat.nb_idx[i, k]] += lat.dx[i, k] * lat.hop[i, k]
+    return D
+
+
+def cheb_T(n, x):
+    return np.cos(n * np.arccos(np.clip(x, -1.0, 1.0)))
+
+
+def eig(Ht):
+    lam, Q = np.linalg.eigh(Ht)
+    return lam, Q
+
+
+def fun_of_h(lam, Q, f):
+    return (Q * f(lam)) @ Q.conj().T
+
+
+def divided_difference(lam, f, fprime):
+    """F_ab = (f(l_a) - f(l_b)) / (l_a - l_b), f'(l_a) when l_a == l_b."""
+    la = lam[:, None]
+    lb = lam[None, :]
+    diff = la - lb
+    close = np.abs(diff) < 1e-9
+    F = np.where(close, 0.0, (f(la) - f(lb)) / np.where(close, 1.0, diff))
+    fp = fprime(0.5 * (la + lb))
+    return np.where(close, fp, F)
+
+
+def frechet(lam, Q, f, fprime, D):
+    """Daleckii-Krein: derivative of f(H) in direction D = Q (F o Q^+ D Q) Q^+."""
+    F = divided_difference(lam, f, fprime)
+    return Q @ (F * (Q.conj().T @ D @ Q)) @ Q.conj().T
