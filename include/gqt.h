@@ -1,0 +1,227 @@
+/*
+ * gqt.h -- C ABI of the GB300 library for linear-scaling Kubo transport.
+ *
+ * The method is that of Fan, Vierimaa and Harju, "GPUQT: An efficient
+ * linear-scaling quantum transport code fully implemented on graphics
+ * processing units" (arXiv:1705.01387): Chebyshev moments of a sparse
+ * tight-binding Hamiltonian applied to random-phase vectors (Sec. 3.1, 3.3),
+ * Chebyshev-Bessel time evolution (Sec. 3.2) and the kernel polynomial method
+ * (Eqs. 25-31), giving the DOS, the velocity autocorrelation (VAC) and the mean
+ * square displacement (MSD), and from them the running conductivity.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  * Units: hbar = e = 1.  H~ = H / dE and dt~ = dE * dt (Eqs. 19-20); dE is
+ *    the handle's energy scale.
+ *  * Device vectors are caller-owned, contiguous, site-major: element (i, r)
+ *    of R vectors sits at index i*R + r.  A vector element is complex:
+ *    two doubles (re, im) for a GQT_FP64 handle, two floats for a
+ *    GQT_FP32_ACC64 handle.  R must be 1, 2, 4, 8, 16 or 32.
+ *  * Random vectors are normalised to 1 per segment (the paper normalises
+ *    <phi|phi> = N, Eq. 13; every moment here is the paper's C_n divided by the
+ *    segment's site count, and gqt_kpm_reconstruct restores the factor).
+ *  * Moment outputs are FP64 and may be host or device memory: a host pointer
+ *    makes the call copy the result back and synchronise the stream before it
+ *    returns; a device pointer leaves the call asynchronous on the stream.
+ *  * "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a call is ordered on that stream.  Calls on
+ *    one handle must not run concurrently (the handle owns its workspace).
+ *  * No entry point aborts, traps or prints.  Errors return a non-zero
+ *    gqt_status and leave a message for gqt_last_error() (thread-local).
+ *    Device-side checks (moment bound, norm, NaN) are read back at the end of
+ *    the call that made them.
+ */
+#ifndef GQT_H
+#define GQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GQT_OK = 0,
+  GQT_EINVAL = 1,   /* bad argument: size, pointer, non-Hermitian input, index out of range */
+  GQT_ENOMEM = 2,   /* device or host allocation failed */
+  GQT_ECUDA = 3,    /* a CUDA runtime call failed (message holds the CUDA error string) */
+  GQT_ERANGE = 4,   /* |mu_m| > |l||r|(1+1e-6): spectrum of H/dE outside [-1,1], dE too small (Sec. 4.2 para.in) */
+  GQT_ENORM = 5,    /* | |U psi| - |psi| | above tolerance after an evolution step */
+  GQT_ENAN = 6,     /* NaN or Inf met in an input or a result */
+  GQT_ETIMEOUT = 7  /* a bounded device wait gave up */
+} gqt_status;
+
+typedef enum { GQT_FP64 = 0, GQT_FP32_ACC64 = 1 } gqt_precision;
+
+typedef enum {
+  GQT_LATTICE_CUSTOM = 0,    /* the paper's input form (neighbour list etc., Sec. 4.2) */
+  GQT_LATTICE_CHAIN = 1,     /* periodic chain, L1 sites, slots +x, -x */
+  GQT_LATTICE_SQUARE = 2,    /* periodic L1 x L2 square lattice, slots +x, -x, +y, -y */
+  GQT_LATTICE_HONEYCOMB = 3, /* periodic L1 x L2 honeycomb cells (2 sites), C-C distance 1 */
+  GQT_LATTICE_CUBIC = 4      /* periodic L1^3 simple cubic, slots +x, -x, +y, -y, +z, -z */
+} gqt_lattice_kind;
+
+/* A tight-binding model (Eq. 32) with positions along the transport direction (Eq. 33).
+ * For the built-in kinds the library generates the lattice itself: hopping t on
+ * every bond, on-site energies W*(u - 1/2) with u from the SplitMix64 stream 1 of
+ * seed, and round(vacancy_frac*N) vacancies (all bonds of the site with the
+ * smallest draws of stream 2 zeroed).  For GQT_LATTICE_CUSTOM, the host arrays
+ * below are read (row-major [n][max_nb]); hop_im may be NULL (real hoppings),
+ * onsite may be NULL (zero), hop_re may be NULL (every listed bond -1, as the
+ * paper's default when hopping.in is absent).  bond_dx[i][k] = X_j - X_i for
+ * the bond to j = nb_idx[i][k], taken as the minimum image under periodic
+ * boundaries (Eq. 34).  Slots k >= nb_count[i] are ignored. */
+typedef struct {
+  int kind;
+  int64_t L1, L2, L3;
+  double t;
+  double W;
+  double vacancy_frac;
+  uint64_t seed;
+  int64_t n;
+  int max_nb;
+  const int32_t* nb_count;
+  const int32_t* nb_idx;
+  const double* hop_re;
+  const double* hop_im;
+  const double* onsite;
+  const double* bond_dx;
+  double length_x;
+  double volume;
+} gqt_lattice;
+
+typedef struct gqt_ham gqt_ham;
+
+/* Build H~ = H/dE on the current CUDA device in ELL form (slot-major arrays,
+ * Sec. 4.2 neighbour list; Eqs. 19, 32-34).  energy_scale <= 0 selects
+ * dE = 1.05 * max_i (|U_i| + sum_k |H_ik|) (Gershgorin bound with 5% margin).
+ * seg_offsets (host, nseg+1 ascending entries from 0 to n) declares a block-
+ * diagonal batch of independent realisations; NULL / nseg <= 1 means one.
+ * Moments are then reduced per segment.  The input must be Hermitian:
+ * H_ji = conj(H_ij) and dx_ji = -dx_ij for every listed bond (EINVAL
+ * otherwise), bonds may not cross segments, and indices must lie in [0, n).
+ * On success *out owns the device arrays until gqt_free_hamiltonian. */
+gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double energy_scale, gqt_precision precision,
+                                 const int64_t* seg_offsets, int nseg, gqt_ham** out);
+void gqt_free_hamiltonian(gqt_ham* ham);
+
+/* The model a built-in lattice kind generates, in the input form (row-major
+ * [n][K] host arrays, caller-allocated; any output may be NULL).  Lets a
+ * caller see exactly which H, positions and disorder gqt_build_hamiltonian
+ * uploads for that kind. */
+gqt_status gqt_generate_lattice(const gqt_lattice* lattice, int64_t* n, int* K, int32_t* nb_count, int32_t* nb_idx,
+                                double* hop_re, double* hop_im, double* onsite, double* bond_dx, double* length_x,
+                                double* volume);
+
+/* n = sites, energy_scale = dE, volume = Omega, nseg = segments, hop_real = 1
+ * when every hopping is real (the library then stores real hoppings). Any output
+ * pointer may be NULL. */
+gqt_status gqt_ham_info(const gqt_ham* ham, int64_t* n, double* energy_scale, double* volume, int* nseg,
+                        int* precision, int* hop_real);
+
+/* Random-phase vectors (Sec. 3.1, Eq. 13): phi[i*R + r] = exp(i 2 pi u)/sqrt(n_s),
+ * u = top 53 bits of draw i of SplitMix64 stream (2^20 + first_vector + r) of
+ * seed / 2^53, n_s = sites of i's segment.  d_phi: device, [n][R], the
+ * handle's element type. */
+gqt_status gqt_random_phase(const gqt_ham* ham, uint64_t seed, int first_vector, int R, void* d_phi, void* stream);
+
+/* mu[s][r][m] = <l_r| T_m(H~) |r_r> restricted to segment s, m < M (Eqs. 21, 23;
+ * Eq. 28 with l = r).  mu is complex: 2*nseg*R*M doubles, host or device.
+ * d_l, d_r: device [n][R].  Fails with ERANGE if some |mu_m| exceeds
+ * |l||r|(1 + 1e-6) (values are still written). */
+gqt_status gqt_cheb_moments(gqt_ham* ham, const void* d_l, const void* d_r, int R, int M, double* mu, void* stream);
+
+/* DOS moments C_n^DOS (Eq. 28): mu[s][r][m] = Re <phi|T_m(H~)|phi>, nseg*R*M doubles. */
+gqt_status gqt_dos_moments(gqt_ham* ham, const void* d_phi, int R, int M, double* mu, void* stream);
+
+/* In place psi <- U(sign*dt) psi (Eq. 17): sum over m < Np of
+ * (2 - delta_m0) (-sign i)^m J_m(dE dt) T_m(H~) psi.  Np <= 0 selects
+ * Np = 1 + max{m : |J_m(dE dt)| >= 1e-15} (machine precision, Sec. 3.2),
+ * capped at 4096.  The Bessel sum accumulates in FP64.  norm (host, [nseg*R]
+ * or NULL) receives |U psi| per segment and vector; the call fails with ENORM
+ * if it differs from |psi| by more than 1e-10 (FP64) / 1e-5 (FP32). */
+gqt_status gqt_evolve(gqt_ham* ham, void* d_psi, int R, double dt, int sign, int Np, double* norm, void* stream);
+
+/* d_out = [X, U(dt)] d_psi (Eqs. 18, 22, 24), [X,H~]_ij = -dx_ij H~_ij; Np as in gqt_evolve. */
+gqt_status gqt_commutator_evolve(gqt_ham* ham, const void* d_psi, void* d_out, int R, double dt, int Np,
+                                 void* stream);
+
+/* d_y = V d_x with V = i sum (X_n - X_m) H_mn |m><n| (Eq. 34).  d_x != d_y. */
+gqt_status gqt_apply_velocity(gqt_ham* ham, const void* d_x, void* d_y, int R, void* stream);
+
+/* VAC state set-up: d_a = phi, d_b = V phi. */
+gqt_status gqt_vac_init(gqt_ham* ham, const void* d_phi, void* d_a, void* d_b, int R, void* stream);
+
+/* VAC moments (Eq. 29).  On entry (d_a, d_b) = (U(-t) phi, U(-t) V phi) at some t;
+ * for k < Nt: row k = Re <V a| T_n(H~) |b>, then a, b <- U(-dt[k]) (a, b).  So rows
+ * are at t, t+dt_0, ..., and on return the state is at t + sum dt (resumable).
+ * dt: host [Nt]; Np: host [Nt] or NULL (rule of gqt_evolve).
+ * mu: [Nt][nseg][R][M] doubles, host or device. */
+gqt_status gqt_vac_moments(gqt_ham* ham, void* d_a, void* d_b, int R, const double* dt, const int* Np, int Nt,
+                           int M, double* mu, void* stream);
+
+/* MSD state set-up: d_p = phi, d_px = 0. */
+gqt_status gqt_msd_init(gqt_ham* ham, const void* d_phi, void* d_p, void* d_px, int R, void* stream);
+
+/* MSD moments (Eq. 30).  On entry (d_p, d_px) = (U(t) phi, [X, U(t)] phi); for k < Nt:
+ * px <- [X, U(dt_k)] p + U(dt_k) px, p <- U(dt_k) p (Eqs. 17-18), then row k =
+ * Re <px| T_n(H~) |px>.  Rows are at t + dt_0, ..., t + sum dt.  Layout as VAC. */
+gqt_status gqt_msd_moments(gqt_ham* ham, void* d_p, void* d_px, int R, const double* dt, const int* Np, int Nt,
+                           int M, double* mu, void* stream);
+
+/* Kernel-polynomial reconstruction (Eqs. 25-27, Jackson damping Eq. 31):
+ * out[row][e] = 2 n_over_omega / (pi dE sqrt(1 - x^2)) * sum_{n<M} g_n (2 - delta_n0) T_n(x) mu[row][n],
+ * x = E[e]/dE, g_n = (1 - n a) cos(pi n a) + a sin(pi n a) cot(pi a), a = 1/(M+1).
+ * n_over_omega = N/Omega (sites per volume).  |x| >= 1 gives NaN.  kernel: 0 =
+ * Jackson, 1 = none (g_n = 1).  d_mu [rows][M], d_E [NE], d_out [rows][NE]:
+ * device FP64. */
+gqt_status gqt_kpm_reconstruct(const double* d_mu, int rows, int M, const double* d_E, int NE, double energy_scale,
+                               double n_over_omega, int kernel, double* d_out, void* stream);
+
+/* Running conductivity from the VAC (Eq. 2): sigma[k][e] = sum_{j<k} dt[j] (v[j][e] + v[j+1][e]) / 2
+ * over rows at t_0 = 0 .. t_{Nt-1} of rho*C_vv (device [Nt][NE]); dt host [Nt]. */
+gqt_status gqt_sigma_vac(const double* d_vac, const double* dt, int Nt, int NE, double* d_sigma, void* stream);
+
+/* Running conductivity from the MSD (Eq. 5): sigma[k][e] = (m[k][e] - m[k-1][e]) / (2 dt[k]),
+ * m[-1] = 0, over rows at t_1 .. t_Nt of rho*dX^2 (device [Nt][NE]). */
+gqt_status gqt_sigma_msd(const double* d_msd, const double* dt, int Nt, int NE, double* d_sigma, void* stream);
+
+/* Reverse-mode gradient of J = sum_k sum_n beta[k][n] C_n^VAC(t_k) (Eq. 29 moments with
+ * rows at t_0 = 0 .. t_{Nt-1}, one vector, one segment).  The paper has no
+ * derivatives; this differentiates its VAC moments, including the dependence of
+ * V on H (Eq. 34), with dE held fixed.  beta: host [Nt][M].  Outputs (device
+ * FP64): d_g_onsite [n] = dJ/dU_i; d_g_slot [n][max_nb] complex G_ik with
+ * dJ = Re sum conj(G_ik) dH_{i,idx(i,k)} over slots, every slot independent
+ * (a real bond's hopping t_ij has dJ/dt = Re(G_ij + G_ji)).  *loss receives J.
+ * Intermediate Chebyshev vectors are recomputed from checkpoints taken every
+ * `stride` orders (stride <= 0: ceil(sqrt(M))). */
+gqt_status gqt_vac_loss_grad(gqt_ham* ham, const void* d_phi, const double* dt, const int* Np, int Nt, int M,
+                             const double* beta, int stride, double* loss, double* d_g_onsite, double* d_g_slot,
+                             void* stream);
+
+/* Host-side Bessel coefficients J_m(x), m < count (Miller backward recurrence
+ * normalised by J_0 + 2 sum J_2k = 1), and the expansion-length rule used when
+ * Np <= 0.  x >= 0. */
+gqt_status gqt_bessel(double x, int count, double* J);
+int gqt_np_rule(double x, int cap);
+
+/* Kernel launch shape for a handle: threads per block and blocks per SM of the
+ * Chebyshev kernels (0 = library default).  gqt_autotune times the candidates
+ * on a scratch copy of one Chebyshev step for the given R and keeps the fastest. */
+gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
+gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, void* stream);
+
+/* Use CUDA graphs for repeated loops (default 1). */
+gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
+
+/* Number of kernel launches the library has enqueued since load (for accounting). */
+uint64_t gqt_launch_count(void);
+
+const char* gqt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GQT_H */

@@ -1,0 +1,761 @@
+// gqt_host.cu -- host runtime behind the C ABI of include/gqt.h.
+//
+// Owns the device copy of H~ (one allocation per array, ELL slot-major),
+// per-handle workspace that grows on demand, the CTA-to-sites tables, CUDA
+// graphs of repeated loops, and the drivers of the DOS, VAC and MSD loops of
+// arXiv:1705.01387 (Sec. 3, Eqs. 17-30).  No entry point aborts: every failure
+// becomes a gqt_status plus a thread-local message.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gqt.h"
+#include "gqt_internal.h"
+#include "gqt_kernels.cuh"
+
+using namespace gqt;
+
+namespace gqt {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+void set_error(const std::string& s) { g_last_error = s; }
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw Error(GQT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void check_launch(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(GQT_ECUDA, std::string("launch ") + what + ": " + cudaGetErrorString(e));
+}
+
+DevBuf::~DevBuf() {
+  if (p) cudaFree(p);
+}
+void DevBuf::ensure(size_t n) {
+  if (n <= bytes) return;
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    throw Error(GQT_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  bytes = n;
+}
+
+// ------------------------------------------------------------ Bessel (host)
+
+// J_m(x), m < count, by Miller's backward recurrence J_{m-1} = (2m/x) J_m - J_{m+1}
+// started far above max(count, x) and normalised with J_0 + 2 sum_k J_2k = 1.
+void bessel_miller(double x, int count, double* J) {
+  if (count <= 0) return;
+  if (x == 0.0) {
+    for (int m = 0; m < count; ++m) J[m] = (m == 0) ? 1.0 : 0.0;
+    return;
+  }
+  const int top = std::max(count, (int)x) + 40 + (int)(6.0 * std::cbrt(x));
+  const int start = top + (top & 1);  // even
+  std::vector<double> j(start + 2, 0.0);
+  j[start + 1] = 0.0;
+  j[start] = 1e-300;
+  double norm = 0.0;
+  for (int m = start; m >= 1; --m) {
+    j[m - 1] = (2.0 * m / x) * j[m] - j[m + 1];
+    if (std::fabs(j[m - 1]) > 1e250) {  // rescale to stay in range
+      for (int q = m - 1; q <= start; ++q) j[q] *= 1e-250;
+    }
+  }
+  norm = j[0];
+  for (int m = 2; m <= start; m += 2) norm += 2.0 * j[m];
+  for (int m = 0; m < count; ++m) J[m] = j[m] / norm;
+}
+
+int np_rule_lib(double x, int cap) {
+  const int probe = std::max(cap, (int)x + 64) + 64;
+  std::vector<double> J(probe);
+  bessel_miller(x, probe, J.data());
+  int last = 0;
+  for (int m = 0; m < probe; ++m)
+    if (std::fabs(J[m]) >= 1e-15) last = m;
+  return std::min(last + 1, cap);
+}
+
+// (2 - delta_m0) (-sign i)^m J_m(x), m < Np  (Eq. 17)
+std::vector<double2> evolve_coefs(double x, int sign, int Np) {
+  std::vector<double> J(Np);
+  bessel_miller(x, Np, J.data());
+  std::vector<double2> c(Np);
+  for (int m = 0; m < Np; ++m) {
+    const double f = (m == 0 ? 1.0 : 2.0) * J[m];
+    // (-sign i)^m : m mod 4 cycle of (1, -sign i, -1, sign i)
+    double re = 0, im = 0;
+    switch (m & 3) {
+      case 0: re = 1; break;
+      case 1: im = -sign; break;
+      case 2: re = -1; break;
+      case 3: im = sign; break;
+    }
+    c[m] = make_double2(f * re, f * im);
+  }
+  return c;
+}
+
+}  // namespace gqt
+
+// ====================================================================== handle
+
+static bool is_pow2_r(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
+
+// dynamic shared memory of the CTA reductions (NV values per vector per warp)
+static size_t smem_bytes(const gqt_ham* h, int R, int nv) { return (size_t)nv * (h->threads / 32) * R * sizeof(double2); }
+
+static int rshift_of(int R) {
+  int s = 0;
+  while ((1 << s) < R) ++s;
+  return s;
+}
+
+const BlockTable& gqt_ham::table(int R) {
+  auto it = tables.find(R);
+  if (it != tables.end()) return *it->second;
+  auto t = std::make_unique<BlockTable>();
+  const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 4;
+  const int thr = threads;
+  const long long max_blocks = (long long)sm_count() * per_sm;
+  // at least ~2 elements per thread per CTA
+  const long long want = std::max<long long>(nseg, std::min<long long>(max_blocks, (n * (long long)R + 2LL * thr - 1) / (2LL * thr)));
+  std::vector<int> blk{0}, seg_blk{0};
+  for (int s = 0; s < nseg; ++s) {
+    const int64_t a = seg[s], b = seg[s + 1];
+    const int64_t ns = b - a;
+    long long nb = std::max<long long>(1, (long long)std::llround((double)want * (double)ns / (double)n));
+    nb = std::min<long long>(nb, std::max<int64_t>(1, ns));
+    for (long long q = 1; q <= nb; ++q) blk.push_back((int)(a + (ns * q) / nb));
+    seg_blk.push_back((int)blk.size() - 1);
+  }
+  t->nblocks = (int)blk.size() - 1;
+  t->d_blk.ensure(blk.size() * sizeof(int));
+  t->d_seg_blk.ensure(seg_blk.size() * sizeof(int));
+  check_cuda(cudaMemcpy(t->d_blk.p, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice), "table");
+  check_cuda(cudaMemcpy(t->d_seg_blk.p, seg_blk.data(), seg_blk.size() * sizeof(int), cudaMemcpyHostToDevice), "table");
+  auto& ref = *t;
+  tables[R] = std::move(t);
+  return ref;
+}
+
+DevBuf& gqt_ham::ws(int slot, size_t bytes) {
+  if ((int)work.size() <= slot) work.resize(slot + 1);
+  if (!work[slot]) work[slot] = std::make_unique<DevBuf>();
+  work[slot]->ensure(bytes);
+  return *work[slot];
+}
+
+// ====================================================================== dispatch helpers
+
+template <bool FP64, bool CH>
+static Ell<FP64, CH> ell_of(const gqt_ham* h) {
+  Ell<FP64, CH> e;
+  e.n = (int)h->n;
+  e.K = h->K;
+  e.idx = (const int*)h->d_idx.p;
+  e.hop2 = (const typename Ell<FP64, CH>::HT*)h->d_hop.p;
+  e.diag2 = (const typename Ell<FP64, CH>::S*)h->d_diag.p;
+  e.dx = (const typename Ell<FP64, CH>::S*)h->d_dx.p;
+  return e;
+}
+
+template <class F>
+static void dispatch(const gqt_ham* h, F&& f) {
+  if (h->prec == GQT_FP64) {
+    if (h->hop_real)
+      f(ell_of<true, false>(h));
+    else
+      f(ell_of<true, true>(h));
+  } else {
+    if (h->hop_real)
+      f(ell_of<false, false>(h));
+    else
+      f(ell_of<false, true>(h));
+  }
+}
+
+template <class E>
+struct EllTraits;
+template <bool FP64, bool CH>
+struct EllTraits<Ell<FP64, CH>> {
+  static constexpr bool fp64 = FP64;
+  static constexpr bool ch = CH;
+  using V = typename Prec<FP64>::V;
+};
+
+size_t gqt_ham::vec_bytes(int R) const { return (size_t)n * R * (prec == GQT_FP64 ? 16 : 8); }
+
+// ====================================================================== status
+
+static gqt_status finish_call(gqt_ham* h, cudaStream_t st, const char* what) {
+  int flag = 0;
+  check_cuda(cudaMemcpyAsync(h->h_flag, h->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+  check_cuda(cudaStreamSynchronize(st), what);
+  flag = *h->h_flag;
+  if (flag & 4) throw Error(GQT_ENAN, std::string(what) + ": NaN or Inf in a result");
+  if (flag & 2)
+    throw Error(GQT_ERANGE, std::string(what) +
+                                ": a Chebyshev moment exceeds |l||r|: the spectrum of H/dE is not inside [-1,1] "
+                                "(energy scale too small)");
+  if (flag & 8) throw Error(GQT_ENORM, std::string(what) + ": |U psi| differs from |psi| beyond tolerance");
+  if (flag & 16) throw Error(GQT_ETIMEOUT, std::string(what) + ": a bounded device wait gave up");
+  return GQT_OK;
+}
+
+static void reset_flag(gqt_ham* h, cudaStream_t st) {
+  check_cuda(cudaMemsetAsync(h->d_flag.p, 0, sizeof(int), st), "flag reset");
+}
+
+// ====================================================================== moments core
+
+// Launch the M-order moment recursion of r against l into partial slots
+// 0..M-1 (norms in slot M) and reduce into out (mode 0 complex / 1 real),
+// layout [nseg][R][M].
+void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int mode,
+                         cudaStream_t st) {
+  const BlockTable& T = h->table(R);
+  const int nb = T.nblocks, rs = rshift_of(R);
+  const size_t vb = h->vec_bytes(R);
+  void* w1 = h->ws(WS_T1, vb).p;
+  void* w2 = h->ws(WS_T2, vb).p;
+  const int slots = std::max(M, 2) + 1;
+  double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * nb * R * sizeof(double2)).p;
+  const int slot_norm = std::max(M, 2);
+  dispatch(h, [&](auto H) {
+    using Tr = EllTraits<decltype(H)>;
+    using V = typename Tr::V;
+    const V* lv = (const V*)l;
+    const V* rv = (const V*)r;
+    V* W1 = (V*)w1;
+    V* W2 = (V*)w2;
+    k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, rv, nullptr, W1, lv, partial,
+                                                        nb, 0, slot_norm, 1);
+    check_launch("k_cheb(first)");
+    for (int m = 2; m < M; ++m) {
+      const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
+      V* tout = (m % 2 == 1) ? W1 : W2;
+      const V* tm2 = (m == 2) ? rv : tout;
+      k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, tm1, tm2, tout, lv,
+                                                          partial, nb, m, slot_norm, 0);
+      check_launch("k_cheb");
+    }
+  });
+  const size_t total = (size_t)h->nseg * R * M;
+  const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
+  // |mu_m| <= |l||r| (1 + tol): tol 1e-6 for FP64; FP32 storage rounds the vectors, so 1e-3.
+  const double tol = (h->prec == GQT_FP64) ? 1e-6 : 1e-3;
+  k_reduce<<<rb, 256, 0, st>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, slot_norm,
+                               (1.0 + tol) * (1.0 + tol), out, mode, (int*)h->d_flag.p);
+  check_launch("k_reduce");
+}
+
+// ====================================================================== evolution core
+
+// In-place evolution of NSET vector sets (each [n][R]) by U(sign*dt) with Np
+// orders.  Norms before/after are checked on the device against tol.
+template <int NSET>
+static void launch_evolve_sets(gqt_ham* h, void* const* psi, int R, const std::vector<double2>& c, cudaStream_t st,
+                               double* d_norms /* [nseg][R][2*NSET] or null */) {
+  const int Np = (int)c.size();
+  const BlockTable& T = h->table(R);
+  const int nb = T.nblocks, rs = rshift_of(R);
+  const size_t vb = h->vec_bytes(R);
+  void* W1[NSET];
+  void* W2[NSET];
+  double2* ACC[NSET];
+  for (int q = 0; q < NSET; ++q) {
+    W1[q] = h->ws(WS_E1 + 2 * q, vb).p;
+    W2[q] = h->ws(WS_E1 + 2 * q + 1, vb).p;
+    ACC[q] = (double2*)h->ws(WS_ACC0 + q, (size_t)h->n * R * sizeof(double2)).p;
+  }
+  double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)(2 * NSET) * nb * R * sizeof(double2)).p;
+  dispatch(h, [&](auto H) {
+    using Tr = EllTraits<decltype(H)>;
+    using V = typename Tr::V;
+    EvoSets<NSET, Tr::fp64> A;
+    // phase 0: m = 0, 1
+    for (int q = 0; q < NSET; ++q) {
+      A.t1[q] = (const V*)psi[q];
+      A.t2[q] = nullptr;
+      A.out[q] = (V*)W1[q];
+      A.acc[q] = ACC[q];
+      A.fin[q] = (V*)psi[q];
+    }
+    const double2 zero = make_double2(0.0, 0.0);
+    k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, c[0],
+                                                                 Np > 1 ? c[1] : zero, 0, partial, nb, 0);
+    check_launch("k_evolve(0)");
+    if (Np <= 2) {
+      k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, zero, zero, 3,
+                                                                   partial, nb, NSET);
+      check_launch("k_evolve(3)");
+    } else {
+      for (int m = 2; m < Np; ++m) {
+        for (int q = 0; q < NSET; ++q) {
+          V* w1 = (V*)W1[q];
+          V* w2 = (V*)W2[q];
+          A.t1[q] = (m - 1) % 2 == 1 ? w1 : w2;
+          V* o = (m % 2 == 1) ? w1 : w2;
+          A.t2[q] = (m == 2) ? (const V*)psi[q] : o;
+          A.out[q] = o;
+        }
+        const int phase = (m == Np - 1) ? 2 : 1;
+        k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, c[m], zero,
+                                                                     phase, partial, nb, NSET);
+        check_launch("k_evolve");
+      }
+    }
+  });
+  const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
+  k_norm_check<<<1, 256, 0, st>>>(partial, NSET, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, d_norms,
+                                  (int*)h->d_flag.p);
+  check_launch("k_norm_check");
+}
+
+static void launch_msd_step(gqt_ham* h, void* p, void* px, int R, const std::vector<double2>& c, cudaStream_t st) {
+  const int Np = (int)c.size();
+  const BlockTable& T = h->table(R);
+  const int nb = T.nblocks, rs = rshift_of(R);
+  const size_t vb = h->vec_bytes(R);
+  void* U1 = h->ws(WS_E1, vb).p;
+  void* U2 = h->ws(WS_E1 + 1, vb).p;
+  void* Z1 = h->ws(WS_E1 + 2, vb).p;
+  void* Z2 = h->ws(WS_E1 + 3, vb).p;
+  double2* AP = (double2*)h->ws(WS_ACC0, (size_t)h->n * R * sizeof(double2)).p;
+  double2* AX = (double2*)h->ws(WS_ACC0 + 1, (size_t)h->n * R * sizeof(double2)).p;
+  double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)4 * nb * R * sizeof(double2)).p;
+  dispatch(h, [&](auto H) {
+    using Tr = EllTraits<decltype(H)>;
+    using V = typename Tr::V;
+    MsdBufs<Tr::fp64> B;
+    B.u1 = (const V*)p;
+    B.z1 = (const V*)px;
+    B.u2 = nullptr;
+    B.z2 = nullptr;
+    B.uo = (V*)U1;
+    B.zo = (V*)Z1;
+    B.accp = AP;
+    B.accx = AX;
+    B.p = (V*)p;
+    B.px = (V*)px;
+    const double2 zero = make_double2(0.0, 0.0);
+    k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, c[0],
+                                                               Np > 1 ? c[1] : zero, 0, partial, nb, 0);
+    check_launch("k_msd_evolve(0)");
+    if (Np <= 2) {
+      k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, zero, zero, 3,
+                                                                 partial, nb, 2);
+      check_launch("k_msd_evolve(3)");
+    } else {
+      for (int m = 2; m < Np; ++m) {
+        B.u1 = (m - 1) % 2 == 1 ? (const V*)U1 : (const V*)U2;
+        B.z1 = (m - 1) % 2 == 1 ? (const V*)Z1 : (const V*)Z2;
+        V* uo = (m % 2 == 1) ? (V*)U1 : (V*)U2;
+        V* zo = (m % 2 == 1) ? (V*)Z1 : (V*)Z2;
+        B.u2 = (m == 2) ? (const V*)p : uo;
+        B.z2 = (m == 2) ? (const V*)px : zo;
+        B.uo = uo;
+        B.zo = zo;
+        const int phase = (m == Np - 1) ? 2 : 1;
+        k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, c[m], zero,
+                                                                   phase, partial, nb, 2);
+        check_launch("k_msd_evolve");
+      }
+    }
+  });
+  // only |U p| vs |p| is a unitarity check; the px norm changes by construction.
+  const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
+  k_norm_check_msd<<<1, 256, 0, st>>>(partial, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, (int*)h->d_flag.p);
+  check_launch("k_norm_check_msd");
+}
+
+void gqt::launch_velocity(gqt_ham* h, const void* x, void* y, void* ycopy, int R, cudaStream_t st) {
+  const BlockTable& T = h->table(R);
+  const int nb = T.nblocks, rs = rshift_of(R);
+  dispatch(h, [&](auto H) {
+    using Tr = EllTraits<decltype(H)>;
+    using V = typename Tr::V;
+    k_velocity<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, 0.5 * h->dE, (const V*)x,
+                                                             (V*)y, (V*)ycopy);
+    check_launch("k_velocity");
+  });
+}
+
+// ====================================================================== API helpers
+
+#define API_BEGIN try {
+#define API_END                                        \
+  }                                                    \
+  catch (const Error& e) {                             \
+    set_error(e.what());                               \
+    return e.code;                                     \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    set_error("host allocation failed");               \
+    return GQT_ENOMEM;                                 \
+  }                                                    \
+  catch (const std::exception& e) {                    \
+    set_error(std::string("internal error: ") + e.what()); \
+    return GQT_EINVAL;                                 \
+  }                                                    \
+  return GQT_OK;
+
+static void require(bool c, const std::string& msg) {
+  if (!c) throw Error(GQT_EINVAL, msg);
+}
+
+static bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+static void check_common(gqt_ham* h, int R) {
+  require(h != nullptr, "null handle");
+  require(is_pow2_r(R), "R must be 1, 2, 4, 8, 16 or 32");
+  int dev = -1;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  require(dev == h->device, "the current CUDA device is not the handle's device");
+}
+
+// Copy a device result to the caller's pointer (host or device).
+static void deliver(const void* dsrc, double* dst, size_t bytes, cudaStream_t st) {
+  if (is_host_ptr(dst))
+    check_cuda(cudaMemcpyAsync(dst, dsrc, bytes, cudaMemcpyDeviceToHost, st), "result copy");
+  else
+    check_cuda(cudaMemcpyAsync(dst, dsrc, bytes, cudaMemcpyDeviceToDevice, st), "result copy");
+}
+
+static int resolve_np(gqt_ham* h, double dt, int Np) {
+  require(std::isfinite(dt) && dt >= 0.0, "time step must be finite and >= 0");
+  if (Np > 0) return Np;
+  return np_rule_lib(h->dE * dt, 4096);
+}
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char* gqt_last_error(void) { return g_last_error.c_str(); }
+uint64_t gqt_launch_count(void) { return g_launches.load(); }
+
+void gqt_free_hamiltonian(gqt_ham* h) { delete h; }
+
+gqt_status gqt_ham_info(const gqt_ham* h, int64_t* n, double* energy_scale, double* volume, int* nseg, int* precision,
+                        int* hop_real) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  if (n) *n = h->n;
+  if (energy_scale) *energy_scale = h->dE;
+  if (volume) *volume = h->volume;
+  if (nseg) *nseg = h->nseg;
+  if (precision) *precision = h->prec;
+  if (hop_real) *hop_real = h->hop_real ? 1 : 0;
+  API_END
+}
+
+gqt_status gqt_bessel(double x, int count, double* J) {
+  API_BEGIN
+  require(J != nullptr && count >= 0 && std::isfinite(x) && x >= 0.0, "gqt_bessel: bad argument");
+  bessel_miller(x, count, J);
+  API_END
+}
+
+int gqt_np_rule(double x, int cap) {
+  if (!(std::isfinite(x) && x >= 0.0) || cap <= 0) return 0;
+  return np_rule_lib(x, cap);
+}
+
+gqt_status gqt_set_graphs(gqt_ham* h, int enable) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  h->use_graphs = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_launch(gqt_ham* h, int threads, int blocks_per_sm) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  if (threads <= 0) threads = 256;
+  require(threads % 32 == 0 && threads <= 1024, "threads must be a multiple of 32, at most 1024");
+  require(blocks_per_sm >= 0 && blocks_per_sm <= 32, "blocks_per_sm out of range");
+  h->threads = threads;
+  h->blocks_per_sm = blocks_per_sm;
+  h->tables.clear();
+  h->graphs.clear();
+  API_END
+}
+
+gqt_status gqt_random_phase(const gqt_ham* hc, uint64_t seed, int first_vector, int R, void* d_phi, void* stream) {
+  API_BEGIN
+  gqt_ham* h = const_cast<gqt_ham*>(hc);
+  check_common(h, R);
+  require(d_phi != nullptr && first_vector >= 0, "gqt_random_phase: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint64_t> keys(R);
+  for (int r = 0; r < R; ++r) {
+    const uint64_t stream_id = (1ull << 20) + (uint64_t)first_vector + (uint64_t)r;
+    keys[r] = splitmix_key(seed, stream_id);
+  }
+  std::vector<double> inv(h->nseg);
+  for (int s = 0; s < h->nseg; ++s) inv[s] = 1.0 / std::sqrt((double)(h->seg[s + 1] - h->seg[s]));
+  DevBuf& dk = h->ws(WS_SMALL0, keys.size() * 8 + inv.size() * 8);
+  check_cuda(cudaMemcpyAsync(dk.p, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, st), "keys");
+  check_cuda(cudaMemcpyAsync((char*)dk.p + keys.size() * 8, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, st),
+             "norms");
+  const size_t total = (size_t)h->n * R;
+  const int nbk = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 8);
+  if (h->prec == GQT_FP64)
+    k_random_phase<true><<<nbk, 256, 0, st>>>((int)h->n, R, (const uint64_t*)dk.p, (const int*)h->d_site_seg.p,
+                                              (const double*)((char*)dk.p + keys.size() * 8), (double2*)d_phi);
+  else
+    k_random_phase<false><<<nbk, 256, 0, st>>>((int)h->n, R, (const uint64_t*)dk.p, (const int*)h->d_site_seg.p,
+                                               (const double*)((char*)dk.p + keys.size() * 8), (float2*)d_phi);
+  check_launch("k_random_phase");
+  check_cuda(cudaStreamSynchronize(st), "gqt_random_phase");
+  API_END
+}
+
+gqt_status gqt_cheb_moments(gqt_ham* h, const void* d_l, const void* d_r, int R, int M, double* mu, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_l && d_r && mu && M >= 1, "gqt_cheb_moments: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  const size_t bytes = (size_t)h->nseg * R * M * sizeof(double2);
+  DevBuf& out = h->ws(WS_MU, bytes);
+  launch_moments(h, d_l, d_r, R, M, out.p, 0, st);
+  deliver(out.p, mu, bytes, st);
+  return finish_call(h, st, "gqt_cheb_moments");
+  API_END
+}
+
+gqt_status gqt_dos_moments(gqt_ham* h, const void* d_phi, int R, int M, double* mu, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_phi && mu && M >= 1, "gqt_dos_moments: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  const size_t bytes = (size_t)h->nseg * R * M * sizeof(double);
+  if (is_host_ptr(mu)) {
+    DevBuf& out = h->ws(WS_MU, bytes);
+    launch_moments(h, d_phi, d_phi, R, M, out.p, 1, st);
+    deliver(out.p, mu, bytes, st);
+  } else {
+    launch_moments(h, d_phi, d_phi, R, M, mu, 1, st);
+  }
+  return finish_call(h, st, "gqt_dos_moments");
+  API_END
+}
+
+gqt_status gqt_evolve(gqt_ham* h, void* d_psi, int R, double dt, int sign, int Np, double* norm, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_psi && (sign == 1 || sign == -1), "gqt_evolve: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Np = resolve_np(h, dt, Np);
+  reset_flag(h, st);
+  const auto c = evolve_coefs(h->dE * dt, sign, Np);
+  DevBuf& dn = h->ws(WS_NORMS, (size_t)h->nseg * R * 2 * sizeof(double));
+  void* sets[1] = {d_psi};
+  launch_evolve_sets<1>(h, sets, R, c, st, (double*)dn.p);
+  gqt_status s = GQT_OK;
+  std::vector<double> hn((size_t)h->nseg * R * 2);
+  check_cuda(cudaMemcpyAsync(hn.data(), dn.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "norms");
+  s = finish_call(h, st, "gqt_evolve");
+  if (norm)
+    for (size_t q = 0; q < (size_t)h->nseg * R; ++q) norm[q] = std::sqrt(hn[2 * q + 1]);
+  return s;
+  API_END
+}
+
+gqt_status gqt_commutator_evolve(gqt_ham* h, const void* d_psi, void* d_out, int R, double dt, int Np,
+                                 void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_psi && d_out && d_psi != d_out, "gqt_commutator_evolve: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Np = resolve_np(h, dt, Np);
+  reset_flag(h, st);
+  const auto c = evolve_coefs(h->dE * dt, +1, Np);
+  // [X,U]psi = the px output of one MSD step started from (p, px) = (psi, 0).
+  const size_t vb = h->vec_bytes(R);
+  void* p = h->ws(WS_P, vb).p;
+  check_cuda(cudaMemcpyAsync(p, d_psi, vb, cudaMemcpyDeviceToDevice, st), "copy");
+  check_cuda(cudaMemsetAsync(d_out, 0, vb, st), "memset");
+  launch_msd_step(h, p, d_out, R, c, st);
+  return finish_call(h, st, "gqt_commutator_evolve");
+  API_END
+}
+
+gqt_status gqt_apply_velocity(gqt_ham* h, const void* d_x, void* d_y, int R, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_x && d_y && d_x != d_y, "gqt_apply_velocity: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  launch_velocity(h, d_x, d_y, nullptr, R, st);
+  return finish_call(h, st, "gqt_apply_velocity");
+  API_END
+}
+
+gqt_status gqt_vac_init(gqt_ham* h, const void* d_phi, void* d_a, void* d_b, int R, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_phi && d_a && d_b && d_phi != d_b && d_a != d_b, "gqt_vac_init: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  launch_velocity(h, d_phi, d_b, d_a == d_phi ? nullptr : d_a, R, st);
+  return finish_call(h, st, "gqt_vac_init");
+  API_END
+}
+
+gqt_status gqt_msd_init(gqt_ham* h, const void* d_phi, void* d_p, void* d_px, int R, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_phi && d_p && d_px && d_p != d_px, "gqt_msd_init: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vb = h->vec_bytes(R);
+  if (d_p != d_phi) check_cuda(cudaMemcpyAsync(d_p, d_phi, vb, cudaMemcpyDeviceToDevice, st), "copy");
+  check_cuda(cudaMemsetAsync(d_px, 0, vb, st), "memset");
+  check_cuda(cudaStreamSynchronize(st), "gqt_msd_init");
+  API_END
+}
+
+gqt_status gqt_vac_moments(gqt_ham* h, void* d_a, void* d_b, int R, const double* dt, const int* Np, int Nt, int M,
+                           double* mu, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_a && d_b && d_a != d_b && dt && mu && Nt >= 0 && M >= 1, "gqt_vac_moments: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  const size_t row = (size_t)h->nseg * R * M;
+  const bool host = is_host_ptr(mu);
+  double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
+  void* l = h->ws(WS_L, h->vec_bytes(R)).p;
+  for (int k = 0; k < Nt; ++k) {
+    const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
+    const auto c = evolve_coefs(h->dE * dt[k], -1, np);
+    launch_velocity(h, d_a, l, nullptr, R, st);
+    launch_moments(h, l, d_b, R, M, dmu + k * row, 1, st);
+    void* sets[2] = {d_a, d_b};
+    launch_evolve_sets<2>(h, sets, R, c, st, nullptr);
+  }
+  if (host && Nt > 0) deliver(dmu, mu, Nt * row * sizeof(double), st);
+  return finish_call(h, st, "gqt_vac_moments");
+  API_END
+}
+
+gqt_status gqt_msd_moments(gqt_ham* h, void* d_p, void* d_px, int R, const double* dt, const int* Np, int Nt, int M,
+                           double* mu, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  require(d_p && d_px && d_p != d_px && dt && mu && Nt >= 0 && M >= 1, "gqt_msd_moments: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  const size_t row = (size_t)h->nseg * R * M;
+  const bool host = is_host_ptr(mu);
+  double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
+  for (int k = 0; k < Nt; ++k) {
+    const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
+    const auto c = evolve_coefs(h->dE * dt[k], +1, np);
+    launch_msd_step(h, d_p, d_px, R, c, st);
+    launch_moments(h, d_px, d_px, R, M, dmu + k * row, 1, st);
+  }
+  if (host && Nt > 0) deliver(dmu, mu, Nt * row * sizeof(double), st);
+  return finish_call(h, st, "gqt_msd_moments");
+  API_END
+}
+
+gqt_status gqt_kpm_reconstruct(const double* d_mu, int rows, int M, const double* d_E, int NE, double energy_scale,
+                               double n_over_omega, int kernel, double* d_out, void* stream) {
+  API_BEGIN
+  require(d_mu && d_E && d_out && rows >= 0 && M >= 1 && NE >= 0 && energy_scale > 0 && (kernel == 0 || kernel == 1),
+          "gqt_kpm_reconstruct: bad argument");
+  if (rows == 0 || NE == 0) return GQT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* tab = nullptr;
+  check_cuda(cudaMallocAsync((void**)&tab, (size_t)M * NE * sizeof(double), st), "cudaMallocAsync");
+  const size_t total = (size_t)M * NE;
+  k_kpm_table<<<(int)std::min<size_t>((total + 255) / 256, 8192), 256, 0, st>>>(M, d_E, NE, energy_scale, n_over_omega,
+                                                                                 kernel == 0, tab);
+  check_launch("k_kpm_table");
+  dim3 grid((NE + 15) / 16, (rows + 15) / 16);
+  k_kpm_gemm<<<grid, 256, 0, st>>>(d_mu, rows, M, tab, NE, d_out);
+  check_launch("k_kpm_gemm");
+  check_cuda(cudaFreeAsync(tab, st), "cudaFreeAsync");
+  check_cuda(cudaStreamSynchronize(st), "gqt_kpm_reconstruct");
+  API_END
+}
+
+static gqt_status sigma_common(const double* d_in, const double* dt, int Nt, int NE, double* d_out, void* stream,
+                               bool vac) {
+  require(d_in && dt && d_out && Nt >= 0 && NE >= 0, "gqt_sigma: bad argument");
+  if (Nt == 0 || NE == 0) return GQT_OK;
+  for (int k = 0; k < Nt; ++k) require(std::isfinite(dt[k]) && dt[k] > 0, "time steps must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* ddt = nullptr;
+  check_cuda(cudaMallocAsync((void**)&ddt, Nt * sizeof(double), st), "cudaMallocAsync");
+  check_cuda(cudaMemcpyAsync(ddt, dt, Nt * sizeof(double), cudaMemcpyHostToDevice, st), "dt copy");
+  const int nbk = std::max(1, std::min(1024, (NE + 127) / 128));
+  if (vac)
+    k_sigma_vac<<<nbk, 128, 0, st>>>(d_in, ddt, Nt, NE, d_out);
+  else
+    k_sigma_msd<<<nbk, 128, 0, st>>>(d_in, ddt, Nt, NE, d_out);
+  check_launch("k_sigma");
+  check_cuda(cudaFreeAsync(ddt, st), "cudaFreeAsync");
+  check_cuda(cudaStreamSynchronize(st), "gqt_sigma");
+  return GQT_OK;
+}
+
+gqt_status gqt_sigma_vac(const double* d_vac, const double* dt, int Nt, int NE, double* d_sigma, void* stream) {
+  API_BEGIN
+  return sigma_common(d_vac, dt, Nt, NE, d_sigma, stream, true);
+  API_END
+}
+
+gqt_status gqt_sigma_msd(const double* d_msd, const double* dt, int Nt, int NE, double* d_sigma, void* stream) {
+  API_BEGIN
+  return sigma_common(d_msd, dt, Nt, NE, d_sigma, stream, false);
+  API_END
+}
+
+}  // extern "C"

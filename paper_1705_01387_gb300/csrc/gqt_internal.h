@@ -1,0 +1,96 @@
+// gqt_internal.h -- shared declarations of the library's host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/gqt.h"
+
+namespace gqt {
+
+struct Error : std::runtime_error {
+  gqt_status code;
+  Error(gqt_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_error(const std::string& s);
+void check_cuda(cudaError_t e, const char* what);
+void check_launch(const char* what);
+int sm_count();
+
+// Device allocation owned by its holder, grown on demand (contents not kept).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  void ensure(size_t n);
+};
+
+// CTA -> site range table for one vector count R: CTA b owns sites
+// [blk[b], blk[b+1]); the CTAs of segment s are seg_blk[s] .. seg_blk[s+1]-1.
+struct BlockTable {
+  int nblocks = 0;
+  DevBuf d_blk, d_seg_blk;
+};
+
+enum WorkSlot {
+  WS_T1 = 0,
+  WS_T2,
+  WS_L,
+  WS_P,
+  WS_PARTIAL,
+  WS_PARTIAL_EVO,
+  WS_MU,
+  WS_NORMS,
+  WS_SMALL0,
+  WS_ACC0,      // +0, +1
+  WS_E1 = 12,   // +0..+3 evolution Chebyshev buffers
+  WS_ADJ0 = 20  // adjoint workspace slots start here
+};
+
+uint64_t splitmix_mix(uint64_t z);
+uint64_t splitmix_key(uint64_t seed, uint64_t stream);
+void bessel_miller(double x, int count, double* J);
+int np_rule_lib(double x, int cap);
+
+}  // namespace gqt
+
+struct gqt_ham {
+  int device = 0;
+  int64_t n = 0;
+  int K = 0;
+  gqt_precision prec = GQT_FP64;
+  bool hop_real = true;
+  double dE = 1.0;
+  double volume = 0.0;
+  double length_x = 0.0;
+  int nseg = 1;
+  std::vector<int64_t> seg;  // nseg + 1 offsets
+  gqt::DevBuf d_idx, d_hop, d_diag, d_dx, d_site_seg, d_flag;
+  int* h_flag = nullptr;  // pinned
+  int threads = 256;
+  int blocks_per_sm = 0;
+  bool use_graphs = true;
+  std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
+  std::vector<std::unique_ptr<gqt::DevBuf>> work;
+  std::map<std::string, cudaGraphExec_t> graphs;
+
+  const gqt::BlockTable& table(int R);
+  gqt::DevBuf& ws(int slot, size_t bytes);
+  size_t vec_bytes(int R) const;
+  ~gqt_ham();
+};
+
+namespace gqt {
+void launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int mode, cudaStream_t st);
+void launch_velocity(gqt_ham* h, const void* x, void* y, void* ycopy, int R, cudaStream_t st);
+}  // namespace gqt

@@ -1,0 +1,674 @@
+// gqt_kernels.cuh -- device kernels of the GB300 Kubo-transport library.
+//
+// Every kernel streams the Hamiltonian H~ (ELL, slot-major) and the vectors
+// once per Chebyshev order; the grid is a fixed set of CTAs, each owning one
+// contiguous range of sites that never crosses a segment boundary, so moment
+// partial sums are per CTA and per segment and their final reduction is a
+// fixed-order (deterministic) sum.
+//
+// Storage of the scaled Hamiltonian (Eqs. 19, 32):
+//   idx  [K][n] int32      neighbour j of slot k of row i (padding: i itself)
+//   hop2 [K][n] HT         2 * H~_{i,j}  (complex V, or real S when all hoppings are real)
+//   diag2[n]    S          2 * U_i / dE
+//   dx   [K][n] S          X_j - X_i (minimum image; 0 on padding)
+// Storing 2H~ turns the Chebyshev step T_m = 2H~T_{m-1} - T_{m-2} (Eq. 21)
+// into one fused multiply-add chain; T_1 = H~T_0 uses the exact factor 1/2.
+//
+// Vectors: [n][R], element (i, r) at i*R + r, complex V = double2 or float2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace gqt {
+
+template <bool FP64>
+struct Prec;
+template <>
+struct Prec<true> {
+  using S = double;
+  using V = double2;
+};
+template <>
+struct Prec<false> {
+  using S = float;
+  using V = float2;
+};
+
+template <class S, bool CH>
+struct HopT;
+template <class S>
+struct HopT<S, true> {
+  using T = typename Prec<sizeof(S) == 8>::V;
+};
+template <class S>
+struct HopT<S, false> {
+  using T = S;
+};
+
+template <bool FP64, bool CH>
+struct Ell {
+  using S = typename Prec<FP64>::S;
+  using HT = typename HopT<S, CH>::T;
+  int n;
+  int K;
+  const int* __restrict__ idx;
+  const HT* __restrict__ hop2;
+  const S* __restrict__ diag2;
+  const S* __restrict__ dx;
+};
+
+// ---------------------------------------------------------------- arithmetic
+
+__device__ __forceinline__ double2 cmul_acc(double2 acc, double2 h, double2 t) {
+  acc.x = fma(h.x, t.x, acc.x);
+  acc.x = fma(-h.y, t.y, acc.x);
+  acc.y = fma(h.x, t.y, acc.y);
+  acc.y = fma(h.y, t.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 cmul_acc(double2 acc, double h, double2 t) {
+  acc.x = fma(h, t.x, acc.x);
+  acc.y = fma(h, t.y, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cmul_acc(float2 acc, float2 h, float2 t) {
+  acc.x = fmaf(h.x, t.x, acc.x);
+  acc.x = fmaf(-h.y, t.y, acc.x);
+  acc.y = fmaf(h.x, t.y, acc.y);
+  acc.y = fmaf(h.y, t.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cmul_acc(float2 acc, float h, float2 t) {
+  acc.x = fmaf(h, t.x, acc.x);
+  acc.y = fmaf(h, t.y, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
+template <class V>
+__device__ __forceinline__ V from_d2(double2 a);
+template <>
+__device__ __forceinline__ double2 from_d2<double2>(double2 a) {
+  return a;
+}
+template <>
+__device__ __forceinline__ float2 from_d2<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+// acc += c * t with c complex double, t storage precision, acc double2.
+template <class V>
+__device__ __forceinline__ double2 cfma_d(double2 acc, double2 c, V t) {
+  double2 td = to_d2(t);
+  acc.x = fma(c.x, td.x, acc.x);
+  acc.x = fma(-c.y, td.y, acc.x);
+  acc.y = fma(c.x, td.y, acc.y);
+  acc.y = fma(c.y, td.x, acc.y);
+  return acc;
+}
+
+// Dot-product accumulators: conj(l) * t summed over a thread's elements.
+// FP64: plain FMA chains.  FP32: the products and sums run in FP32 with the
+// error-free transformations of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005: TwoProduct by fmaf, TwoSum), and
+// the compensated (hi, lo) pair is folded into an FP64 total every 16 terms,
+// so FP64 work per element stays far below one operation.
+template <class V>
+struct DotAcc;
+
+template <>
+struct DotAcc<double2> {
+  double2 s = make_double2(0.0, 0.0);
+  __device__ __forceinline__ void add(double2 l, double2 t) {
+    s.x = fma(l.x, t.x, s.x);
+    s.x = fma(l.y, t.y, s.x);
+    s.y = fma(l.x, t.y, s.y);
+    s.y = fma(-l.y, t.x, s.y);
+  }
+  __device__ __forceinline__ void add_norm(double2 t) {  // |t|^2 into .x
+    s.x = fma(t.x, t.x, s.x);
+    s.x = fma(t.y, t.y, s.x);
+  }
+  __device__ __forceinline__ double2 get() { return s; }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+struct CompF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo += e + pe;
+  }
+};
+
+template <>
+struct DotAcc<float2> {
+  CompF re, im;
+  double2 s = make_double2(0.0, 0.0);
+  int cnt = 0;
+  __device__ __forceinline__ void flush() {
+    s.x += (double)re.hi + (double)re.lo;
+    s.y += (double)im.hi + (double)im.lo;
+    re = CompF();
+    im = CompF();
+    cnt = 0;
+  }
+  __device__ __forceinline__ void add(float2 l, float2 t) {
+    re.add_prod(l.x, t.x);
+    re.add_prod(l.y, t.y);
+    im.add_prod(l.x, t.y);
+    im.add_prod(-l.y, t.x);
+    if (++cnt == 16) flush();
+  }
+  __device__ __forceinline__ void add_norm(float2 t) {
+    re.add_prod(t.x, t.x);
+    re.add_prod(t.y, t.y);
+    if (++cnt == 16) flush();
+  }
+  __device__ __forceinline__ double2 get() {
+    flush();
+    return s;
+  }
+};
+
+// Dynamic shared memory for the CTA reductions: NV * (blockDim/32) * R double2.
+__device__ __forceinline__ double2* dyn_smem() {
+  extern __shared__ __align__(16) unsigned char gqt_smem_raw[];
+  return reinterpret_cast<double2*>(gqt_smem_raw);
+}
+
+// Sum a per-thread double2 over the threads of a CTA that share the same
+// vector index r (= threadIdx.x & (R-1)); thread r < R of the CTA then holds
+// the CTA total for vector r.  blockDim.x is a multiple of 32, R divides 32.
+template <int NV>
+__device__ __forceinline__ void block_reduce_r(double2 (&v)[NV], int R, double2* smem /*[NV][warps][R]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    for (int off = 16; off >= R; off >>= 1) {
+      v[q].x += __shfl_xor_sync(0xffffffffu, v[q].x, off);
+      v[q].y += __shfl_xor_sync(0xffffffffu, v[q].y, off);
+    }
+  }
+  if (lane < R) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) smem[(q * nw + warp) * R + lane] = v[q];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < R) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int w = 0; w < nw; ++w) {
+        double2 t = smem[(q * nw + w) * R + threadIdx.x];
+        s.x += t.x;
+        s.y += t.y;
+      }
+      v[q] = s;
+    }
+  }
+}
+
+// y = sum_k hop2[k][i] * x[idx[k][i]*R + r] + diag2[i] * x[i*R + r]  (= 2 H~ x, element (i, r)).
+template <bool FP64, bool CH>
+__device__ __forceinline__ typename Prec<FP64>::V apply2h(const Ell<FP64, CH>& H, const typename Prec<FP64>::V* __restrict__ x,
+                                                         int i, int r, int rs, typename Prec<FP64>::V acc) {
+  using V = typename Prec<FP64>::V;
+  acc = cmul_acc(acc, __ldg(H.diag2 + i), __ldg(x + (((size_t)i << rs) + r)));
+  for (int k = 0; k < H.K; ++k) {
+    const size_t s = (size_t)k * H.n + i;
+    const int j = __ldg(H.idx + s);
+    acc = cmul_acc(acc, __ldg(H.hop2 + s), __ldg(x + (((size_t)j << rs) + r)));
+  }
+  return acc;
+}
+
+// y = 2 [X, H~] x  (element (i, r)): [X,H~]_ij = -dx_ij H~_ij.
+template <bool FP64, bool CH>
+__device__ __forceinline__ typename Prec<FP64>::V apply2xh(const Ell<FP64, CH>& H, const typename Prec<FP64>::V* __restrict__ x,
+                                                          int i, int r, int rs, typename Prec<FP64>::V acc) {
+  for (int k = 0; k < H.K; ++k) {
+    const size_t s = (size_t)k * H.n + i;
+    const int j = __ldg(H.idx + s);
+    const auto h = __ldg(H.hop2 + s);
+    const auto d = -__ldg(H.dx + s);
+    acc = cmul_acc(acc, h, cscale(__ldg(x + (((size_t)j << rs) + r)), d));
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------ K2: moments
+
+// One Chebyshev order fused with the moment dot product (Eqs. 21, 28).
+// first != 0: tout = H~ tm1 (T_1 from T_0 = tm1) and partials for m = 0, 1 and
+// the norms (|l|^2, |r|^2) into slots slot0, slot0+1, slot_norm.
+// first == 0: tout = 2 H~ tm1 - tm2 (tout may alias tm2) and the partial of
+// <l|tout> into slot slot0.
+template <bool FP64, bool CH>
+__global__ void k_cheb(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs,
+                       const typename Prec<FP64>::V* __restrict__ tm1, const typename Prec<FP64>::V* tm2,
+                       typename Prec<FP64>::V* tout, const typename Prec<FP64>::V* __restrict__ l,
+                       double2* __restrict__ partial, int nblocks, int slot0, int slot_norm, int first) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  DotAcc<V> d1, d0, nl, nr;
+  for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = (int)(e >> rs);
+    const V lv = __ldg(l + e);
+    if (first) {
+      V zero;
+      zero.x = 0;
+      zero.y = 0;
+      V y = apply2h<FP64, CH>(H, tm1, i, r, rs, zero);
+      y = cscale(y, (S)0.5);
+      tout[e] = y;
+      const V t0 = __ldg(tm1 + e);
+      d0.add(lv, t0);
+      d1.add(lv, y);
+      nl.add_norm(lv);
+      nr.add_norm(t0);
+    } else {
+      V y = apply2h<FP64, CH>(H, tm1, i, r, rs, cneg(tm2[e]));
+      tout[e] = y;
+      d1.add(lv, y);
+    }
+  }
+  if (first) {
+    double2 v[3] = {d0.get(), d1.get(), make_double2(nl.get().x, nr.get().x)};
+    block_reduce_r<3>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(slot0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+      partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
+    }
+  } else {
+    double2 v[1] = {d1.get()};
+    block_reduce_r<1>(v, R, smem);
+    if ((int)threadIdx.x < R) partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+  }
+}
+
+// Deterministic second pass: out[s][r][m] = sum over the segment's CTAs, in
+// CTA order, of partial[m][b][r].  mode 0: complex out (double2), mode 1: real
+// part (double).  Bound check: |mu_m|^2 <= bound_factor |l|^2 |r|^2 (norms
+// from slot slot_norm), failure sets bit 1 of *flag; NaN/Inf sets bit 2.
+__global__ void k_reduce(const double2* __restrict__ partial, int nslots_m, int nblocks, int R,
+                         const int* __restrict__ seg_blk, int nseg, int slot_norm, double bound_factor, void* out,
+                         int mode, int* __restrict__ flag) {
+  const size_t total = (size_t)nseg * R * nslots_m;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % R);
+    const int m = (int)((t / R) % nslots_m);
+    const int s = (int)(t / ((size_t)R * nslots_m));
+    double2 acc = make_double2(0.0, 0.0);
+    double2 nrm = make_double2(0.0, 0.0);
+    for (int b = seg_blk[s]; b < seg_blk[s + 1]; ++b) {
+      const double2 p = partial[((size_t)m * nblocks + b) * R + r];
+      acc.x += p.x;
+      acc.y += p.y;
+      if (slot_norm >= 0) {
+        const double2 q = partial[((size_t)slot_norm * nblocks + b) * R + r];
+        nrm.x += q.x;
+        nrm.y += q.y;
+      }
+    }
+    const size_t o = ((size_t)s * R + r) * nslots_m + m;
+    if (mode == 0)
+      reinterpret_cast<double2*>(out)[o] = acc;
+    else
+      reinterpret_cast<double*>(out)[o] = acc.x;
+    if (!isfinite(acc.x) || !isfinite(acc.y)) atomicOr(flag, 4);
+    if (slot_norm >= 0) {
+      const double bound = nrm.x * nrm.y * bound_factor + 1e-300;
+      if (acc.x * acc.x + acc.y * acc.y > bound) atomicOr(flag, 2);
+    }
+  }
+}
+
+// ------------------------------------------------------------ K3: evolution
+
+// Chebyshev-Bessel evolution (Eq. 17) of NSET independent vector sets that
+// share H~.  Order m of the recursion on set q: t1[q] holds T_{m-1} psi, t2[q]
+// T_{m-2} psi (tm2 may be the input psi itself for m = 2), out[q] receives T_m
+// psi.  acc[q] (FP64) accumulates c_m T_m psi.
+//   phase 0 (m = 0, 1): out = H~ psi; acc = c0 psi + c1 out; norm partials of psi.
+//   phase 1 (2 <= m < Np-1): out = 2H~t1 - t2; acc += c_m out.
+//   phase 2 (m = Np-1): psi_final = acc + c_m (2H~t1 - t2) written to fin[q]
+//            (storage precision) and its norm partials.
+//   phase 3 (finish, Np <= 2): fin = acc, norm partials.
+template <int NSET, bool FP64>
+struct EvoSets {
+  const typename Prec<FP64>::V* t1[NSET];
+  const typename Prec<FP64>::V* t2[NSET];
+  typename Prec<FP64>::V* out[NSET];
+  double2* acc[NSET];
+  typename Prec<FP64>::V* fin[NSET];
+};
+
+template <int NSET, bool FP64, bool CH>
+__global__ void k_evolve(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs, EvoSets<NSET, FP64> A,
+                         double2 c0, double2 c1, int phase, double2* __restrict__ partial, int nblocks, int slot) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  DotAcc<V> nrm[NSET];
+  for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = (int)(e >> rs);
+#pragma unroll
+    for (int q = 0; q < NSET; ++q) {
+      if (phase == 0) {
+        V zero;
+        zero.x = 0;
+        zero.y = 0;
+        V y = cscale(apply2h<FP64, CH>(H, A.t1[q], i, r, rs, zero), (S)0.5);
+        A.out[q][e] = y;
+        const V p = __ldg(A.t1[q] + e);
+        double2 a = cfma_d(make_double2(0.0, 0.0), c0, p);
+        A.acc[q][e] = cfma_d(a, c1, y);
+        nrm[q].add_norm(p);
+      } else if (phase == 1) {
+        V y = apply2h<FP64, CH>(H, A.t1[q], i, r, rs, cneg(A.t2[q][e]));
+        A.out[q][e] = y;
+        A.acc[q][e] = cfma_d(A.acc[q][e], c0, y);
+      } else if (phase == 2) {
+        V y = apply2h<FP64, CH>(H, A.t1[q], i, r, rs, cneg(A.t2[q][e]));
+        V f = from_d2<V>(cfma_d(A.acc[q][e], c0, y));
+        A.fin[q][e] = f;
+        nrm[q].add_norm(f);
+      } else {
+        V f = from_d2<V>(A.acc[q][e]);
+        A.fin[q][e] = f;
+        nrm[q].add_norm(f);
+      }
+    }
+  }
+  if (phase != 1) {
+    double2 v[NSET];
+#pragma unroll
+    for (int q = 0; q < NSET; ++q) v[q] = nrm[q].get();
+    block_reduce_r<NSET>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+#pragma unroll
+      for (int q = 0; q < NSET; ++q) partial[((size_t)(slot + q) * nblocks + b) * R + threadIdx.x] = v[q];
+    }
+  }
+}
+
+// ------------------------------------------------ K4: commutator evolution
+
+// One order of the coupled recursions behind one MSD time step (Eqs. 17, 18,
+// 22, 24): with p = T_0 input and px the current [X,U(t)]phi,
+//   u_m = T_m(H~) p            (u_0 = p, u_1 = H~ p)
+//   z_m = [X, T_m] p + T_m px  (z_0 = px, z_1 = [X,H~] p + H~ px)
+//   z_m = 2[X,H~] u_{m-1} + 2H~ z_{m-1} - z_{m-2}  (sum of Eq. 22 and Eq. 21)
+// and accp += c_m u_m (-> U(dt) p), accx += c_m z_m (-> [X,U(dt)]p + U(dt)px).
+// phase 0: m = 0, 1; phase 1: middle orders; phase 2: last order, writes
+// p <- U p, px <- [X,U]p + U px (storage precision); phase 3: finish from acc.
+template <bool FP64>
+struct MsdBufs {
+  const typename Prec<FP64>::V* u1;
+  const typename Prec<FP64>::V* u2;
+  typename Prec<FP64>::V* uo;
+  const typename Prec<FP64>::V* z1;
+  const typename Prec<FP64>::V* z2;
+  typename Prec<FP64>::V* zo;
+  double2* accp;
+  double2* accx;
+  typename Prec<FP64>::V* p;
+  typename Prec<FP64>::V* px;
+};
+
+template <bool FP64, bool CH>
+__global__ void k_msd_evolve(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs, MsdBufs<FP64> B, double2 c0,
+                             double2 c1, int phase, double2* __restrict__ partial, int nblocks, int slot) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  DotAcc<V> n0, n1;
+  V zero;
+  zero.x = 0;
+  zero.y = 0;
+  for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = (int)(e >> rs);
+    if (phase == 0) {
+      // u1 = H~ p ; z1 = [X,H~] p + H~ px ; inputs: B.u1 = p, B.z1 = px
+      V u = cscale(apply2h<FP64, CH>(H, B.u1, i, r, rs, zero), (S)0.5);
+      V z = apply2xh<FP64, CH>(H, B.u1, i, r, rs, zero);
+      z = cscale(apply2h<FP64, CH>(H, B.z1, i, r, rs, z), (S)0.5);
+      B.uo[e] = u;
+      B.zo[e] = z;
+      const V p0 = __ldg(B.u1 + e), x0 = __ldg(B.z1 + e);
+      B.accp[e] = cfma_d(cfma_d(make_double2(0.0, 0.0), c0, p0), c1, u);
+      B.accx[e] = cfma_d(cfma_d(make_double2(0.0, 0.0), c0, x0), c1, z);
+      n0.add_norm(p0);
+    } else if (phase == 3) {
+      V p = from_d2<V>(B.accp[e]);
+      V x = from_d2<V>(B.accx[e]);
+      B.p[e] = p;
+      B.px[e] = x;
+      n0.add_norm(p);
+      n1.add_norm(x);
+    } else {
+      V u = apply2h<FP64, CH>(H, B.u1, i, r, rs, cneg(B.u2[e]));
+      V z = apply2xh<FP64, CH>(H, B.u1, i, r, rs, cneg(B.z2[e]));
+      z = apply2h<FP64, CH>(H, B.z1, i, r, rs, z);
+      if (phase == 1) {
+        B.uo[e] = u;
+        B.zo[e] = z;
+        B.accp[e] = cfma_d(B.accp[e], c0, u);
+        B.accx[e] = cfma_d(B.accx[e], c0, z);
+      } else {
+        V p = from_d2<V>(cfma_d(B.accp[e], c0, u));
+        V x = from_d2<V>(cfma_d(B.accx[e], c0, z));
+        B.p[e] = p;
+        B.px[e] = x;
+        n0.add_norm(p);
+        n1.add_norm(x);
+      }
+    }
+  }
+  if (phase != 1) {
+    double2 v[2] = {n0.get(), n1.get()};
+    block_reduce_r<2>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)slot * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(slot + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+    }
+  }
+}
+
+// Norm check of an evolution: slots q (before) and NSET + q (after) hold the
+// partial squared norms of set q.  | |after| - |before| | > tol |before| sets
+// bit 3 of *flag.  norms (optional) receives [nseg][R][NSET][2] squared norms.
+__global__ void k_norm_check(const double2* __restrict__ partial, int nset, int nblocks, int R,
+                             const int* __restrict__ seg_blk, int nseg, double tol, double* __restrict__ norms,
+                             int* __restrict__ flag) {
+  const int total = nseg * R * nset;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int q = t % nset, r = (t / nset) % R, s = t / (nset * R);
+    double a = 0.0, z = 0.0;
+    for (int b = seg_blk[s]; b < seg_blk[s + 1]; ++b) {
+      a += partial[((size_t)q * nblocks + b) * R + r].x;
+      z += partial[((size_t)(nset + q) * nblocks + b) * R + r].x;
+    }
+    if (norms) {
+      norms[(size_t)t * 2] = a;
+      norms[(size_t)t * 2 + 1] = z;
+    }
+    if (!isfinite(z)) atomicOr(flag, 4);
+    if (fabs(sqrt(z) - sqrt(a)) > tol * sqrt(a) + 1e-300) atomicOr(flag, 8);
+  }
+}
+
+// MSD step: slot 0 = |p|^2 before, slot 2 = |U p|^2 after (slot 3 = |px|^2, unchecked).
+__global__ void k_norm_check_msd(const double2* __restrict__ partial, int nblocks, int R,
+                                 const int* __restrict__ seg_blk, int nseg, double tol, int* __restrict__ flag) {
+  const int total = nseg * R;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int r = t % R, s = t / R;
+    double a = 0.0, z = 0.0, x = 0.0;
+    for (int b = seg_blk[s]; b < seg_blk[s + 1]; ++b) {
+      a += partial[((size_t)0 * nblocks + b) * R + r].x;
+      z += partial[((size_t)2 * nblocks + b) * R + r].x;
+      x += partial[((size_t)3 * nblocks + b) * R + r].x;
+    }
+    if (!isfinite(z) || !isfinite(x)) atomicOr(flag, 4);
+    if (fabs(sqrt(z) - sqrt(a)) > tol * sqrt(a) + 1e-300) atomicOr(flag, 8);
+  }
+}
+
+// --------------------------------------------------------------- K5: velocity
+
+// y = V x = i dE sum_k dx_ik H~_ik x_j (Eq. 34); with hop2 = 2H~ the factor is i dE/2.
+template <bool FP64, bool CH>
+__global__ void k_velocity(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs, double half_dE,
+                           const typename Prec<FP64>::V* __restrict__ x, typename Prec<FP64>::V* __restrict__ y,
+                           typename Prec<FP64>::V* __restrict__ y2 /* optional copy of x */) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = (int)(e >> rs);
+    V a;
+    a.x = 0;
+    a.y = 0;
+    for (int k = 0; k < H.K; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      const int j = __ldg(H.idx + s);
+      a = cmul_acc(a, __ldg(H.hop2 + s), cscale(__ldg(x + (((size_t)j << rs) + r)), __ldg(H.dx + s)));
+    }
+    // multiply by i * dE/2
+    V o;
+    o.x = -a.y * (S)half_dE;
+    o.y = a.x * (S)half_dE;
+    y[e] = o;
+    if (y2) y2[e] = __ldg(x + e);
+  }
+}
+
+// --------------------------------------------------------------- K7: KPM
+
+// tab[n][e] = g_n (2 - delta_n0) cos(n arccos x_e) * 2 n_over_omega / (pi dE sqrt(1 - x_e^2))
+// (Eqs. 25-27, 31); NaN where |x_e| >= 1.
+__global__ void k_kpm_table(int M, const double* __restrict__ E, int NE, double dE, double n_over_omega, int jackson,
+                            double* __restrict__ tab) {
+  const size_t total = (size_t)M * NE;
+  const double a = 1.0 / (M + 1.0);
+  const double cot = cos(M_PI * a) / sin(M_PI * a);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int e = (int)(t % NE);
+    const int n = (int)(t / NE);
+    const double x = E[e] / dE;
+    double v;
+    if (!(fabs(x) < 1.0)) {
+      v = CUDART_NAN;
+    } else {
+      const double g = jackson ? (1.0 - n * a) * cos(M_PI * n * a) + a * sin(M_PI * n * a) * cot : 1.0;
+      v = g * (n == 0 ? 1.0 : 2.0) * cos(n * acos(x)) * 2.0 * n_over_omega / (M_PI * dE * sqrt(1.0 - x * x));
+    }
+    tab[t] = v;
+  }
+}
+
+// out[row][e] = sum_n mu[row][n] tab[n][e]: a small FP64 GEMM, 16x16 tiles.
+__global__ void k_kpm_gemm(const double* __restrict__ mu, int rows, int M, const double* __restrict__ tab, int NE,
+                           double* __restrict__ out) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < M; k0 += 16) {
+    As[ty][tx] = (row < rows && k0 + tx < M) ? mu[(size_t)row * M + k0 + tx] : 0.0;
+    Bs[ty][tx] = (k0 + ty < M && col < NE) ? tab[(size_t)(k0 + ty) * NE + col] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
+  }
+  if (row < rows && col < NE) out[(size_t)row * NE + col] = acc;
+}
+
+// --------------------------------------------------------------- sigma
+
+__global__ void k_sigma_vac(const double* __restrict__ v, const double* __restrict__ dt, int Nt, int NE,
+                            double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NE; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    out[e] = 0.0;
+    for (int k = 1; k < Nt; ++k) {
+      s += 0.5 * dt[k - 1] * (v[(size_t)(k - 1) * NE + e] + v[(size_t)k * NE + e]);
+      out[(size_t)k * NE + e] = s;
+    }
+  }
+}
+
+__global__ void k_sigma_msd(const double* __restrict__ m, const double* __restrict__ dt, int Nt, int NE,
+                            double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NE; e += gridDim.x * blockDim.x) {
+    double prev = 0.0;
+    for (int k = 0; k < Nt; ++k) {
+      const double c = m[(size_t)k * NE + e];
+      out[(size_t)k * NE + e] = (c - prev) / (2.0 * dt[k]);
+      prev = c;
+    }
+  }
+}
+
+// --------------------------------------------------------------- random phase
+
+// SplitMix64 (Steele, Lea, Flood 2014): draw i of the stream keyed by
+// key = mix(seed + (stream+1) G) is mix(key + (i+1) G).
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <bool FP64>
+__global__ void k_random_phase(int n, int R, const uint64_t* __restrict__ keys, const int* __restrict__ site_seg,
+                               const double* __restrict__ seg_inv_sqrt, typename Prec<FP64>::V* __restrict__ phi) {
+  using V = typename Prec<FP64>::V;
+  const size_t total = (size_t)n * R;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / R), r = (int)(t % R);
+    const uint64_t z = sm64_mix(keys[r] + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+    const double u = (double)(z >> 11) * 0x1.0p-53;
+    double s, c;
+    sincospi(2.0 * u, &s, &c);
+    const double w = seg_inv_sqrt[site_seg ? site_seg[i] : 0];
+    V v;
+    v.x = c * w;
+    v.y = s * w;
+    phi[t] = v;
+  }
+}
+
+}  // namespace gqt
