@@ -1,0 +1,299 @@
+"""Benchmark of the Kubo-transport hot path on GB300.
+
+Default workload (one GPU): the FP64 honeycomb lattice of 4096 x 2048 cells
+(N = 16,777,216 orbitals, t = -2.7 eV, Anderson disorder in [-1, 1] eV,
+dE = 9.555 eV), one random-phase vector, M = 3000 Chebyshev moments, time step
+dt = 2 hbar/|t| (N_p = 29 Bessel orders).  One step = one time step of the VAC
+and MSD runs: the VAC row (velocity, M fused Chebyshev orders against V a) and
+the U(-dt) evolution of (a, b); the MSD step (coupled [X,U] evolution of
+(p, p_X)) and its row (M orders); and the kernel-polynomial reconstruction of
+both rows on 1001 energies.  Metric: orbital-moments per second, N * 2M per
+step.  ``--impl reference`` times the serial FP64 oracle on the host cores on
+a bounded sample of the same workload (a few moments at full N).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gqt_synth as S  # noqa: E402
+
+METRIC = "orbital-moments/s (H.phi products)"
+UNIT = "orbital*moments/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def workload(small: bool):
+    w = S.config(1, small=small)
+    lat = S.build_lattice(w.lattice_args, w.seed)
+    return w, lat
+
+
+def bytes_per_orbital_cheb(K: int, fp64: bool, hop_real: bool, R: int) -> float:
+    """Algorithmic bytes per orbital per Chebyshev order of the fused moment kernel:
+    per vector element T_{m-1} (gather counted once), T_{m-2}, T_m, l (4 complex
+    values); H~ once per site: K int32 indices, K hoppings, 1 diagonal."""
+    v = 16 if fp64 else 8
+    s = 8 if fp64 else 4
+    hop = s if hop_real else 2 * s
+    return 4 * v * R + K * (4 + hop) + s
+
+
+def run_ours(args):
+    import torch
+    import paper_1705_01387_gb300 as g
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w, lat = workload(args.small)
+    dE = w.energy_scale
+    ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP64)
+    N, M, R = lat.n, w.M, 1
+    Np = g.gqt_np_rule(dE * w.dt, 64)
+    del lat
+    cd = torch.complex128
+    phi = torch.empty((N, R), dtype=cd, device="cuda")
+    g.gqt_random_phase(ham, w.seed, R, phi, first_vector=rank)
+    a, b, p, px = (torch.empty_like(phi) for _ in range(4))
+    g.gqt_vac_init(ham, phi, a, b, R)
+    g.gqt_msd_init(ham, phi, p, px, R)
+    E = torch.from_numpy(w.energies).cuda()
+    nO = N / ham.volume
+    rows = torch.empty((2, M), dtype=torch.float64, device="cuda")
+    recon = torch.empty((2, E.numel()), dtype=torch.float64, device="cuda")
+    dts = np.array([w.dt])
+
+    def step():
+        g.gqt_vac_moments(ham, a, b, R, dts, M, rows[0], Np=[Np])
+        g.gqt_msd_moments(ham, p, px, R, dts, M, rows[1], Np=[Np])
+        g.gqt_kpm_reconstruct(rows, E, dE, nO, recon)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = g.gqt_launch_count()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        g.gqt_profile_start()
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        prof_ms, prof_n = g.gqt_profile_stop(5)
+    launches = g.gqt_launch_count() - launches0
+    t_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    units = float(N) * 2 * M * args.steps * ws
+    value = units / (t_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: the step's state vectors come
+    # from pinned host memory, the rows and the updated state go back to the host.
+    hs = [torch.empty((N, R), dtype=cd, pin_memory=True) for _ in range(4)]
+    for h_, d_ in zip(hs, (a, b, p, px)):
+        h_.copy_(d_)
+    hrows = np.empty((2, M))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for h_, d_ in zip(hs, (a, b, p, px)):
+            d_.copy_(h_, non_blocking=True)
+        g.gqt_vac_moments(ham, a, b, R, dts, M, hrows[0], Np=[Np])
+        g.gqt_msd_moments(ham, p, px, R, dts, M, hrows[1], Np=[Np])
+        for h_, d_ in zip(hs, (a, b, p, px)):
+            h_.copy_(d_, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    vb = N * R * 16
+    e2e = {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * vb,
+           "d2h_bytes_per_step": 4 * vb + 2 * M * 8}
+
+    # roofline of the dominant kernel: the fused Chebyshev order (SpMV + recurrence + dot)
+    hbm, peak_kind = _peaks()
+    bpo = bytes_per_orbital_cheb(3, True, ham.hop_real, R)
+    n_launch = int(prof_n[1])
+    avg_s = prof_ms[1] * 1e-3 / max(n_launch, 1)
+    achieved = N * bpo / avg_s / 1e9
+    total_prof = float(np.sum(prof_ms))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded Anderson honeycomb lattice and random-phase vectors)",
+        "config": {"workload": w.name if not args.small else w.name + "_small", "n_orbitals": N, "moments": M,
+                   "vectors_per_gpu": R, "bessel_orders": Np, "dt_hbar_per_eV": w.dt, "energies": int(E.numel()),
+                   "step": "one VAC + MSD time step (2M moments, 2 evolutions) + KPM reconstruction",
+                   "hop_storage": "real FP64" if ham.hop_real else "complex FP64",
+                   "l2": "inputs larger than L2 (H~ ELL %.2f GB + state vectors)" % (N * (3 * 12 + 8 + 24) / 1e9),
+                   "parallelism": f"replicas x{ws} (independent random vectors)"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "k_cheb (fused SpMV + three-term recurrence + moment dot)",
+                     "bytes_per_orbital": bpo, "avg_launch_us": avg_s * 1e6, "launches": n_launch,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                     "kernel_share_of_timed": prof_ms[1] / max(total_prof, 1e-12)},
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.small, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample(small: bool):
+    import oracle as O
+    w, lat = workload(small)
+    h = O.Hamiltonian(lat, w.energy_scale)
+    phi = S.random_phase(lat.n, 1, seed=w.seed)[:, 0]
+    return w, lat, h, phi
+
+
+def cpu_baseline(small: bool, budget_s: float = 15.0, prepared=None):
+    """Serial FP64 oracle on one host core: Chebyshev moments at full N, as many
+    as fit in about budget_s seconds, scaled to orbital-moments/s."""
+    w, lat, h, phi = prepared or _oracle_sample(small)
+    t0 = time.perf_counter()
+    h.cheb_moments(phi, phi, 2)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-6)
+    m = int(max(3, min(400, budget_s / per)))
+    t0 = time.perf_counter()
+    h.cheb_moments(phi, phi, m)
+    dt = time.perf_counter() - t0
+    return {"value": lat.n * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{m} Chebyshev moments <phi|T_m(H~)|phi> of the same lattice at full N = {lat.n} "
+                      f"(serial FP64 C++, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    prepared = _oracle_sample(args.small)
+    w, lat = prepared[0], prepared[1]
+    per_step = max(1.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        cpu_baseline(args.small, per_step, prepared)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.small, per_step, prepared))
+    elapsed = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name if not args.small else w.name + "_small", "n_orbitals": lat.n,
+                      "moments": w.M, "step": "bounded sample: serial oracle Chebyshev moments at full N"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": vals[-1]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="reduced lattice, for tests")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

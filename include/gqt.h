@@ -215,6 +215,16 @@ gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, v
 /* Use CUDA graphs for repeated loops (default 1). */
 gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
 
+/* Per-kernel timing with CUDA events on the launch stream.  After
+ * gqt_profile_start every launch of the Chebyshev kernels is bracketed by two
+ * events; gqt_profile_stop waits for them and returns, per family, the summed
+ * milliseconds and the launch count: 0 = first moment order, 1 = moment orders
+ * m >= 2 (the fused SpMV + recurrence + dot kernel), 2 = one-set evolution
+ * order, 3 = two-set evolution order, 4 = coupled commutator order.  Graph
+ * capture is bypassed while profiling. */
+gqt_status gqt_profile_start(void);
+gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);
+
 /* Number of kernel launches the library has enqueued since load (for accounting). */
 uint64_t gqt_launch_count(void);
 

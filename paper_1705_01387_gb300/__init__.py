@@ -63,6 +63,8 @@ _SIGS = {
     "gqt_autotune": [_P, _I, _P, _P, _P],
     "gqt_set_graphs": [_P, _I],
     "gqt_launch_count": [],
+    "gqt_profile_start": [],
+    "gqt_profile_stop": [_P, _P, _I],
     "gqt_last_error": [],
 }
 _RESTYPES = {"gqt_free_hamiltonian": None, "gqt_np_rule": C.c_int, "gqt_launch_count": C.c_uint64,
@@ -327,6 +329,18 @@ def gqt_autotune(ham: Ham, R: int, stream=None):
 
 def gqt_set_graphs(ham: Ham, enable: bool):
     _check(lib().gqt_set_graphs(ham.ptr, int(bool(enable))))
+
+
+def gqt_profile_start():
+    _check(lib().gqt_profile_start())
+
+
+def gqt_profile_stop(ncat: int = 5):
+    """Returns (ms per family, launches per family) since gqt_profile_start."""
+    ms = np.zeros(ncat)
+    n = np.zeros(ncat, np.uint64)
+    _check(lib().gqt_profile_stop(ms.ctypes.data, n.ctypes.data, int(ncat)))
+    return ms, n
 
 
 def gqt_launch_count() -> int:

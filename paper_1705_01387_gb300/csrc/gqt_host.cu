@@ -131,6 +131,40 @@ std::vector<double2> evolve_coefs(double x, int sign, int Np) {
 
 }  // namespace gqt
 
+// ====================================================================== profiler
+
+// Optional per-kernel timing: CUDA events recorded on the launch stream
+// around each launch of the profiled kernel families, summed on read.
+namespace {
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> pairs;  // (category, index of start event)
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+Profiler g_prof;
+}  // namespace
+
+static inline size_t prof_begin(cudaStream_t st) {
+  if (!g_prof.on) return (size_t)-1;
+  size_t i = g_prof.used;
+  check_cuda(cudaEventRecord(g_prof.get(), st), "cudaEventRecord");
+  return i;
+}
+static inline void prof_end(size_t i, int cat, cudaStream_t st) {
+  if (i == (size_t)-1) return;
+  check_cuda(cudaEventRecord(g_prof.get(), st), "cudaEventRecord");
+  g_prof.pairs.push_back({cat, i});
+}
+
 // ====================================================================== handle
 
 static bool is_pow2_r(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
@@ -262,16 +296,20 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
     const V* rv = (const V*)r;
     V* W1 = (V*)w1;
     V* W2 = (V*)w2;
+    size_t pe = prof_begin(st);
     k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, rv, nullptr, W1, lv, partial,
                                                         nb, 0, slot_norm, 1);
     check_launch("k_cheb(first)");
+    prof_end(pe, 0, st);
     for (int m = 2; m < M; ++m) {
       const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
       V* tout = (m % 2 == 1) ? W1 : W2;
       const V* tm2 = (m == 2) ? rv : tout;
+      pe = prof_begin(st);
       k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, tm1, tm2, tout, lv,
                                                           partial, nb, m, slot_norm, 0);
       check_launch("k_cheb");
+      prof_end(pe, 1, st);
     }
   });
   const size_t total = (size_t)h->nseg * R * M;
@@ -334,9 +372,11 @@ static void launch_evolve_sets(gqt_ham* h, void* const* psi, int R, const std::v
           A.out[q] = o;
         }
         const int phase = (m == Np - 1) ? 2 : 1;
+        size_t pe = prof_begin(st);
         k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, c[m], zero,
                                                                      phase, partial, nb, NSET);
         check_launch("k_evolve");
+        prof_end(pe, 1 + NSET, st);
       }
     }
   });
@@ -391,9 +431,11 @@ static void launch_msd_step(gqt_ham* h, void* p, void* px, int R, const std::vec
         B.uo = uo;
         B.zo = zo;
         const int phase = (m == Np - 1) ? 2 : 1;
+        size_t pe = prof_begin(st);
         k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, c[m], zero,
                                                                    phase, partial, nb, 2);
         check_launch("k_msd_evolve");
+        prof_end(pe, 4, st);
       }
     }
   });
@@ -475,6 +517,36 @@ static int resolve_np(gqt_ham* h, double dt, int Np) {
 extern "C" {
 
 const char* gqt_last_error(void) { return g_last_error.c_str(); }
+
+gqt_status gqt_profile_start(void) {
+  API_BEGIN
+  g_prof.on = true;
+  g_prof.used = 0;
+  g_prof.pairs.clear();
+  API_END
+}
+
+gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat) {
+  API_BEGIN
+  require(ncat >= 0 && (ncat == 0 || (ms && launches)), "gqt_profile_stop: bad argument");
+  for (int c = 0; c < ncat; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  for (auto& pr : g_prof.pairs) {
+    check_cuda(cudaEventSynchronize(g_prof.pool[pr.second + 1]), "cudaEventSynchronize");
+    float t = 0.f;
+    check_cuda(cudaEventElapsedTime(&t, g_prof.pool[pr.second], g_prof.pool[pr.second + 1]), "cudaEventElapsedTime");
+    if (pr.first < ncat) {
+      ms[pr.first] += t;
+      launches[pr.first] += 1;
+    }
+  }
+  g_prof.on = false;
+  g_prof.used = 0;
+  g_prof.pairs.clear();
+  API_END
+}
 uint64_t gqt_launch_count(void) { return g_launches.load(); }
 
 void gqt_free_hamiltonian(gqt_ham* h) { delete h; }
