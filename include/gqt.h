@@ -225,6 +225,30 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);
 
+/* DOS moments (same result as gqt_dos_moments) for callers that cannot allocate
+ * device memory: callers whose device memory belongs to another allocator (a
+ * framework's caching pool, a fixed budget) that must not be bypassed, and
+ * callers on latency-critical paths where cudaMalloc/cudaFree would synchronise
+ * the device.  The paper has no counterpart; this is a deployment variant of the
+ * fused moment kernel.  The call allocates nothing: its scratch (two Chebyshev
+ * vectors, per-CTA partial sums, CTA table, status word) lives in one fixed
+ * file-scope device array of GQT_NOALLOC_SCRATCH_BYTES bytes, which every GPU
+ * that loads the library holds until the process exits.
+ *  - Limit: 2*n*R*e + (max(M,2)+1)*nb*R*16 + a few KB must fit in the array
+ *    (e = 16 bytes FP64 / 8 bytes FP32 per element, nb = min(2*SMs,
+ *    ceil(n*R/1024)) CTAs); larger requests return GQT_EINVAL naming the size.
+ *  - Single-segment handles only.  d_phi: device [n][R]; d_mu: DEVICE memory,
+ *    nseg*R*M doubles (Re <phi|T_m|phi>); the handle must have been built earlier.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array and it keeps the previous call's contents
+ *    (the call re-initialises what must start at zero); calls whose GPU work
+ *    overlaps (other streams, other threads) race on it and must be serialised.
+ *  - The call waits for its stream before returning (status check). */
+#define GQT_NOALLOC_SCRATCH_BYTES (4u << 20)
+gqt_status gqt_dos_moments_noalloc(const gqt_ham* ham, const void* d_phi, int R, int M, double* d_mu, void* stream);
+
 /* Number of kernel launches the library has enqueued since load (for accounting). */
 uint64_t gqt_launch_count(void);
 

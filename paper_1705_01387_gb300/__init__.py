@@ -66,6 +66,7 @@ _SIGS = {
     "gqt_profile_start": [],
     "gqt_profile_stop": [_P, _P, _I],
     "gqt_last_error": [],
+    "gqt_dos_moments_noalloc": [_P, _P, _I, _I, _P, _P],
 }
 _RESTYPES = {"gqt_free_hamiltonian": None, "gqt_np_rule": C.c_int, "gqt_launch_count": C.c_uint64,
              "gqt_last_error": C.c_char_p}
@@ -217,6 +218,14 @@ def gqt_cheb_moments(ham: Ham, l, r, R: int, M: int, mu, stream=None):
 
 def gqt_dos_moments(ham: Ham, phi, R: int, M: int, mu, stream=None):
     _check(lib().gqt_dos_moments(ham.ptr, _dptr(phi, "phi"), int(R), int(M), _out_ptr(mu), _stream(stream)))
+    return mu
+
+
+def gqt_dos_moments_noalloc(ham: Ham, phi, R: int, M: int, mu, stream=None):
+    """As gqt_dos_moments, for callers that may not allocate device memory: mu must be a
+    float64 CUDA tensor; scratch comes from the library's fixed device array."""
+    _check(lib().gqt_dos_moments_noalloc(ham.ptr, _dptr(phi, "phi"), int(R), int(M), _dptr(mu, "mu"),
+                                         _stream(stream)))
     return mu
 
 
