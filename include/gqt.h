@@ -179,6 +179,14 @@ gqt_status gqt_msd_moments(gqt_ham* ham, void* d_p, void* d_px, int R, const dou
 gqt_status gqt_kpm_reconstruct(const double* d_mu, int rows, int M, const double* d_E, int NE, double energy_scale,
                                double n_over_omega, int kernel, double* d_out, void* stream);
 
+/* Transpose of gqt_kpm_reconstruct: d_beta[n] = sum_e w[e] * (the coefficient of mu[n]
+ * in out[e]), so that sum_e w[e] out[row][e] = sum_n d_beta[n] mu[row][n].  Turns an
+ * energy-weighted loss on reconstructed DOS/VAC/MSD values into moment weights
+ * (the beta of gqt_vac_loss_grad).  Energies with |E| >= dE must have w = 0.
+ * d_E, d_w [NE], d_beta [M]: device FP64. */
+gqt_status gqt_kpm_weights(int M, const double* d_E, int NE, const double* d_w, double energy_scale,
+                           double n_over_omega, int kernel, double* d_beta, void* stream);
+
 /* Running conductivity from the VAC (Eq. 2): sigma[k][e] = sum_{j<k} dt[j] (v[j][e] + v[j+1][e]) / 2
  * over rows at t_0 = 0 .. t_{Nt-1} of rho*C_vv (device [Nt][NE]); dt host [Nt]. */
 gqt_status gqt_sigma_vac(const double* d_vac, const double* dt, int Nt, int NE, double* d_sigma, void* stream);
@@ -219,8 +227,9 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
  * gqt_profile_start every launch of the Chebyshev kernels is bracketed by two
  * events; gqt_profile_stop waits for them and returns, per family, the summed
  * milliseconds and the launch count: 0 = first moment order, 1 = moment orders
- * m >= 2 (the fused SpMV + recurrence + dot kernel), 2 = one-set evolution
- * order, 3 = two-set evolution order, 4 = coupled commutator order.  Graph
+ * m >= 2 with l != r (the fused SpMV + recurrence + dot kernel), 2 = one-set
+ * evolution order, 3 = two-set evolution order, 4 = coupled commutator order,
+ * 5 = moment steps m >= 2 with l = r (two moments per step).  Graph
  * capture is bypassed while profiling. */
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);

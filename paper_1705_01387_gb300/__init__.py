@@ -54,6 +54,7 @@ _SIGS = {
     "gqt_msd_init": [_P, _P, _P, _P, _I, _P],
     "gqt_msd_moments": [_P, _P, _P, _I, _P, _P, _I, _I, _P, _P],
     "gqt_kpm_reconstruct": [_P, _I, _I, _P, _I, _D, _D, _I, _P, _P],
+    "gqt_kpm_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _P],
     "gqt_sigma_vac": [_P, _P, _I, _I, _P, _P],
     "gqt_sigma_msd": [_P, _P, _I, _I, _P, _P],
     "gqt_vac_loss_grad": [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P],
@@ -288,6 +289,13 @@ def gqt_kpm_reconstruct(mu, E, energy_scale: float, n_over_omega: float, out, ke
                                      float(energy_scale), float(n_over_omega), int(kernel), _dptr(out, "out"),
                                      _stream(stream)))
     return out
+
+
+def gqt_kpm_weights(M: int, E, w, energy_scale: float, n_over_omega: float, beta, kernel: int = 0, stream=None):
+    """beta[n] = sum_e w[e] d(reconstructed value at E[e]) / d(mu_n); E, w, beta CUDA float64."""
+    _check(lib().gqt_kpm_weights(int(M), _dptr(E, "E"), int(E.numel()), _dptr(w, "w"), float(energy_scale),
+                                 float(n_over_omega), int(kernel), _dptr(beta, "beta"), _stream(stream)))
+    return beta
 
 
 def gqt_sigma_vac(vac, dt, out, stream=None):

@@ -239,6 +239,9 @@ gqt_ham::~gqt_ham() {
   for (auto& g : graphs)
     if (g.second) cudaGraphExecDestroy(g.second);
   if (h_flag) cudaFreeHost(h_flag);
+  if (gstream) cudaStreamDestroy(gstream);
+  for (auto e : gev)
+    if (e) cudaEventDestroy(e);
 }
 
 extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double energy_scale, gqt_precision precision,

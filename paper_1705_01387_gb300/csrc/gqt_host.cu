@@ -165,6 +165,83 @@ static inline void prof_end(size_t i, int cat, cudaStream_t st) {
   g_prof.pairs.push_back({cat, i});
 }
 
+// ====================================================================== graphs
+
+// Replays a loop of launches as a CUDA graph keyed by everything the launches
+// depend on (kind, sizes, pointers, coefficients).  Capture and replay run on
+// the handle's own non-blocking stream, ordered after and before the caller's
+// stream by events, so the caller may pass the legacy default stream.
+template <class F>
+static void run_graph(gqt_ham* h, const std::string& key, cudaStream_t st, F&& launches) {
+  if (!h->use_graphs || g_prof.on) {
+    launches(st);
+    return;
+  }
+  if (!h->gstream) {
+    check_cuda(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
+    check_cuda(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming), "cudaEventCreate");
+    check_cuda(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming), "cudaEventCreate");
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 256) {
+      for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+      h->graphs.clear();
+    }
+    cudaGraph_t graph = nullptr;
+    check_cuda(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    try {
+      launches(h->gstream);
+    } catch (...) {
+      cudaStreamEndCapture(h->gstream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    check_cuda(cudaStreamEndCapture(h->gstream, &graph), "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    check_cuda(e, "cudaGraphInstantiate");
+    it = h->graphs.emplace(key, exec).first;
+  }
+  check_cuda(cudaEventRecord(h->gev[0], st), "cudaEventRecord");
+  check_cuda(cudaStreamWaitEvent(h->gstream, h->gev[0], 0), "cudaStreamWaitEvent");
+  check_cuda(cudaGraphLaunch(it->second, h->gstream), "cudaGraphLaunch");
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  check_cuda(cudaEventRecord(h->gev[1], h->gstream), "cudaEventRecord");
+  check_cuda(cudaStreamWaitEvent(st, h->gev[1], 0), "cudaStreamWaitEvent");
+}
+
+static std::string key_of(const char* op, std::initializer_list<const void*> ptrs, std::initializer_list<double> nums) {
+  std::string k(op);
+  char buf[64];
+  for (auto p : ptrs) {
+    snprintf(buf, sizeof buf, "|%p", p);
+    k += buf;
+  }
+  for (auto x : nums) {
+    snprintf(buf, sizeof buf, "|%.17g", x);
+    k += buf;
+  }
+  return k;
+}
+
+// The exact bits of every expansion coefficient, as part of a graph key (a
+// lossy hash can map U(+dt) and U(-dt), whose coefficients differ only in
+// signs, to the same key).
+static std::string coef_bits(const std::vector<double2>& c) {
+  std::string k("|c");
+  char buf[40];
+  for (const double2& q : c) {
+    uint64_t u[2];
+    memcpy(u, &q, 16);
+    snprintf(buf, sizeof buf, "%016llx%016llx", (unsigned long long)u[0], (unsigned long long)u[1]);
+    k += buf;
+  }
+  return k;
+}
+
 // ====================================================================== handle
 
 static bool is_pow2_r(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
@@ -276,49 +353,88 @@ static void reset_flag(gqt_ham* h, cudaStream_t st) {
 
 // ====================================================================== moments core
 
-// Launch the M-order moment recursion of r against l into partial slots
-// 0..M-1 (norms in slot M) and reduce into out (mode 0 complex / 1 real),
-// layout [nseg][R][M].
-void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int mode,
+// Launch the moment recursion of r against l and reduce into out, layout
+// [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
+// (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
+// (ceil(M/2) recursion steps, double out).
+void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int kind,
                          cudaStream_t st) {
   const BlockTable& T = h->table(R);
   const int nb = T.nblocks, rs = rshift_of(R);
   const size_t vb = h->vec_bytes(R);
   void* w1 = h->ws(WS_T1, vb).p;
   void* w2 = h->ws(WS_T2, vb).p;
-  const int slots = std::max(M, 2) + 1;
+  const int slots = std::max(M, 2) + 2;
   double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * nb * R * sizeof(double2)).p;
   const int slot_norm = std::max(M, 2);
-  dispatch(h, [&](auto H) {
-    using Tr = EllTraits<decltype(H)>;
-    using V = typename Tr::V;
-    const V* lv = (const V*)l;
-    const V* rv = (const V*)r;
-    V* W1 = (V*)w1;
-    V* W2 = (V*)w2;
-    size_t pe = prof_begin(st);
-    k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, rv, nullptr, W1, lv, partial,
-                                                        nb, 0, slot_norm, 1);
-    check_launch("k_cheb(first)");
-    prof_end(pe, 0, st);
-    for (int m = 2; m < M; ++m) {
-      const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
-      V* tout = (m % 2 == 1) ? W1 : W2;
-      const V* tm2 = (m == 2) ? rv : tout;
-      pe = prof_begin(st);
-      k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, tm1, tm2, tout, lv,
-                                                          partial, nb, m, slot_norm, 0);
-      check_launch("k_cheb");
-      prof_end(pe, 1, st);
-    }
-  });
-  const size_t total = (size_t)h->nseg * R * M;
-  const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
   // |mu_m| <= |l||r| (1 + tol): tol 1e-6 for FP64; FP32 storage rounds the vectors, so 1e-3.
   const double tol = (h->prec == GQT_FP64) ? 1e-6 : 1e-3;
-  k_reduce<<<rb, 256, 0, st>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, slot_norm,
-                               (1.0 + tol) * (1.0 + tol), out, mode, (int*)h->d_flag.p);
-  check_launch("k_reduce");
+  const size_t total = (size_t)h->nseg * R * M;
+  const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
+  const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p},
+                                 {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb});
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    dispatch(h, [&](auto H) {
+      using Tr = EllTraits<decltype(H)>;
+      using V = typename Tr::V;
+      const V* lv = (const V*)l;
+      const V* rv = (const V*)r;
+      V* W1 = (V*)w1;
+      V* W2 = (V*)w2;
+      const int* blk = (const int*)T.d_blk.p;
+      if (kind == 2) {
+        const int steps = (M + 1) / 2;  // step m yields moments 2m-2 and 2m-1
+        size_t pe = prof_begin(s2);
+        k_cheb_dbl<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1,
+                                                                                  partial, nb, 1);
+        check_launch("k_cheb_dbl(first)");
+        prof_end(pe, 0, s2);
+        for (int m = 2; m <= std::max(steps, 1); ++m) {
+          const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
+          V* tout = (m % 2 == 1) ? W1 : W2;
+          const V* tm2 = (m == 2) ? rv : tout;
+          pe = prof_begin(s2);
+          k_cheb_dbl<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout,
+                                                                                    partial, nb, m);
+          check_launch("k_cheb_dbl");
+          prof_end(pe, 5, s2);
+        }
+        return;
+      }
+      size_t pe = prof_begin(s2);
+      if (kind == 0)
+        k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1, lv,
+                                                                              partial, nb, 0, slot_norm, 1);
+      else
+        k_cheb_re<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1, lv,
+                                                                                 partial, nb, 0, slot_norm, 1);
+      check_launch("k_cheb(first)");
+      prof_end(pe, 0, s2);
+      for (int m = 2; m < M; ++m) {
+        const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
+        V* tout = (m % 2 == 1) ? W1 : W2;
+        const V* tm2 = (m == 2) ? rv : tout;
+        pe = prof_begin(s2);
+        if (kind == 0)
+          k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout, lv,
+                                                                                partial, nb, m, slot_norm, 0);
+        else
+          k_cheb_re<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout, lv,
+                                                                                   partial, nb, m, slot_norm, 0);
+        check_launch("k_cheb");
+        prof_end(pe, 1, s2);
+      }
+    });
+    if (kind == 2) {
+      k_reduce_dbl<<<rb, 256, 0, s2>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, 1.0 + tol, (double*)out,
+                                       (int*)h->d_flag.p);
+      check_launch("k_reduce_dbl");
+    } else {
+      k_reduce<<<rb, 256, 0, s2>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, slot_norm,
+                                   (1.0 + tol) * (1.0 + tol), out, kind == 0 ? 0 : 1, (int*)h->d_flag.p);
+      check_launch("k_reduce");
+    }
+  });
 }
 
 // ====================================================================== evolution core
@@ -341,49 +457,54 @@ static void launch_evolve_sets(gqt_ham* h, void* const* psi, int R, const std::v
     ACC[q] = (double2*)h->ws(WS_ACC0 + q, (size_t)h->n * R * sizeof(double2)).p;
   }
   double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)(2 * NSET) * nb * R * sizeof(double2)).p;
-  dispatch(h, [&](auto H) {
-    using Tr = EllTraits<decltype(H)>;
-    using V = typename Tr::V;
-    EvoSets<NSET, Tr::fp64> A;
-    // phase 0: m = 0, 1
-    for (int q = 0; q < NSET; ++q) {
-      A.t1[q] = (const V*)psi[q];
-      A.t2[q] = nullptr;
-      A.out[q] = (V*)W1[q];
-      A.acc[q] = ACC[q];
-      A.fin[q] = (V*)psi[q];
-    }
-    const double2 zero = make_double2(0.0, 0.0);
-    k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, c[0],
-                                                                 Np > 1 ? c[1] : zero, 0, partial, nb, 0);
-    check_launch("k_evolve(0)");
-    if (Np <= 2) {
-      k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, zero, zero, 3,
-                                                                   partial, nb, NSET);
-      check_launch("k_evolve(3)");
-    } else {
-      for (int m = 2; m < Np; ++m) {
-        for (int q = 0; q < NSET; ++q) {
-          V* w1 = (V*)W1[q];
-          V* w2 = (V*)W2[q];
-          A.t1[q] = (m - 1) % 2 == 1 ? w1 : w2;
-          V* o = (m % 2 == 1) ? w1 : w2;
-          A.t2[q] = (m == 2) ? (const V*)psi[q] : o;
-          A.out[q] = o;
-        }
-        const int phase = (m == Np - 1) ? 2 : 1;
-        size_t pe = prof_begin(st);
-        k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, A, c[m], zero,
-                                                                     phase, partial, nb, NSET);
-        check_launch("k_evolve");
-        prof_end(pe, 1 + NSET, st);
+  const std::string cbits = coef_bits(c);
+  const std::string key = key_of("evo", {psi[0], psi[NSET - 1], W1[0], W2[0], ACC[0], partial, d_norms, T.d_blk.p},
+                                 {(double)NSET, (double)R, (double)Np, (double)h->threads}) + cbits;
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    dispatch(h, [&](auto H) {
+      using Tr = EllTraits<decltype(H)>;
+      using V = typename Tr::V;
+      EvoSets<NSET, Tr::fp64> A;
+      // phase 0: m = 0, 1
+      for (int q = 0; q < NSET; ++q) {
+        A.t1[q] = (const V*)psi[q];
+        A.t2[q] = nullptr;
+        A.out[q] = (V*)W1[q];
+        A.acc[q] = ACC[q];
+        A.fin[q] = (V*)psi[q];
       }
-    }
+      const double2 zero = make_double2(0.0, 0.0);
+      k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, A, c[0],
+                                                                   Np > 1 ? c[1] : zero, 0, partial, nb, 0);
+      check_launch("k_evolve(0)");
+      if (Np <= 2) {
+        k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, A, zero, zero, 3,
+                                                                     partial, nb, NSET);
+        check_launch("k_evolve(3)");
+      } else {
+        for (int m = 2; m < Np; ++m) {
+          for (int q = 0; q < NSET; ++q) {
+            V* w1 = (V*)W1[q];
+            V* w2 = (V*)W2[q];
+            A.t1[q] = (m - 1) % 2 == 1 ? w1 : w2;
+            V* o = (m % 2 == 1) ? w1 : w2;
+            A.t2[q] = (m == 2) ? (const V*)psi[q] : o;
+            A.out[q] = o;
+          }
+          const int phase = (m == Np - 1) ? 2 : 1;
+          size_t pe = prof_begin(s2);
+          k_evolve<NSET, Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, A, c[m], zero,
+                                                                       phase, partial, nb, NSET);
+          check_launch("k_evolve");
+          prof_end(pe, 1 + NSET, s2);
+        }
+      }
+    });
+    const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
+    k_norm_check<<<1, 256, 0, s2>>>(partial, NSET, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, d_norms,
+                                    (int*)h->d_flag.p);
+    check_launch("k_norm_check");
   });
-  const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
-  k_norm_check<<<1, 256, 0, st>>>(partial, NSET, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, d_norms,
-                                  (int*)h->d_flag.p);
-  check_launch("k_norm_check");
 }
 
 static void launch_msd_step(gqt_ham* h, void* p, void* px, int R, const std::vector<double2>& c, cudaStream_t st) {
@@ -398,51 +519,56 @@ static void launch_msd_step(gqt_ham* h, void* p, void* px, int R, const std::vec
   double2* AP = (double2*)h->ws(WS_ACC0, (size_t)h->n * R * sizeof(double2)).p;
   double2* AX = (double2*)h->ws(WS_ACC0 + 1, (size_t)h->n * R * sizeof(double2)).p;
   double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)4 * nb * R * sizeof(double2)).p;
-  dispatch(h, [&](auto H) {
-    using Tr = EllTraits<decltype(H)>;
-    using V = typename Tr::V;
-    MsdBufs<Tr::fp64> B;
-    B.u1 = (const V*)p;
-    B.z1 = (const V*)px;
-    B.u2 = nullptr;
-    B.z2 = nullptr;
-    B.uo = (V*)U1;
-    B.zo = (V*)Z1;
-    B.accp = AP;
-    B.accx = AX;
-    B.p = (V*)p;
-    B.px = (V*)px;
-    const double2 zero = make_double2(0.0, 0.0);
-    k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, c[0],
-                                                               Np > 1 ? c[1] : zero, 0, partial, nb, 0);
-    check_launch("k_msd_evolve(0)");
-    if (Np <= 2) {
-      k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, zero, zero, 3,
-                                                                 partial, nb, 2);
-      check_launch("k_msd_evolve(3)");
-    } else {
-      for (int m = 2; m < Np; ++m) {
-        B.u1 = (m - 1) % 2 == 1 ? (const V*)U1 : (const V*)U2;
-        B.z1 = (m - 1) % 2 == 1 ? (const V*)Z1 : (const V*)Z2;
-        V* uo = (m % 2 == 1) ? (V*)U1 : (V*)U2;
-        V* zo = (m % 2 == 1) ? (V*)Z1 : (V*)Z2;
-        B.u2 = (m == 2) ? (const V*)p : uo;
-        B.z2 = (m == 2) ? (const V*)px : zo;
-        B.uo = uo;
-        B.zo = zo;
-        const int phase = (m == Np - 1) ? 2 : 1;
-        size_t pe = prof_begin(st);
-        k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), st>>>(H, (const int*)T.d_blk.p, R, rs, B, c[m], zero,
-                                                                   phase, partial, nb, 2);
-        check_launch("k_msd_evolve");
-        prof_end(pe, 4, st);
+  const std::string cbits = coef_bits(c);
+  const std::string key = key_of("msd", {p, px, U1, Z1, AP, AX, partial, T.d_blk.p},
+                                 {(double)R, (double)Np, (double)h->threads}) + cbits;
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    dispatch(h, [&](auto H) {
+      using Tr = EllTraits<decltype(H)>;
+      using V = typename Tr::V;
+      MsdBufs<Tr::fp64> B;
+      B.u1 = (const V*)p;
+      B.z1 = (const V*)px;
+      B.u2 = nullptr;
+      B.z2 = nullptr;
+      B.uo = (V*)U1;
+      B.zo = (V*)Z1;
+      B.accp = AP;
+      B.accx = AX;
+      B.p = (V*)p;
+      B.px = (V*)px;
+      const double2 zero = make_double2(0.0, 0.0);
+      k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, B, c[0],
+                                                                 Np > 1 ? c[1] : zero, 0, partial, nb, 0);
+      check_launch("k_msd_evolve(0)");
+      if (Np <= 2) {
+        k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, B, zero, zero, 3,
+                                                                   partial, nb, 2);
+        check_launch("k_msd_evolve(3)");
+      } else {
+        for (int m = 2; m < Np; ++m) {
+          B.u1 = (m - 1) % 2 == 1 ? (const V*)U1 : (const V*)U2;
+          B.z1 = (m - 1) % 2 == 1 ? (const V*)Z1 : (const V*)Z2;
+          V* uo = (m % 2 == 1) ? (V*)U1 : (V*)U2;
+          V* zo = (m % 2 == 1) ? (V*)Z1 : (V*)Z2;
+          B.u2 = (m == 2) ? (const V*)p : uo;
+          B.z2 = (m == 2) ? (const V*)px : zo;
+          B.uo = uo;
+          B.zo = zo;
+          const int phase = (m == Np - 1) ? 2 : 1;
+          size_t pe = prof_begin(s2);
+          k_msd_evolve<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, (const int*)T.d_blk.p, R, rs, B, c[m], zero,
+                                                                     phase, partial, nb, 2);
+          check_launch("k_msd_evolve");
+          prof_end(pe, 4, s2);
+        }
       }
-    }
+    });
+    // only |U p| vs |p| is a unitarity check; the px norm changes by construction.
+    const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
+    k_norm_check_msd<<<1, 256, 0, s2>>>(partial, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, (int*)h->d_flag.p);
+    check_launch("k_norm_check_msd");
   });
-  // only |U p| vs |p| is a unitarity check; the px norm changes by construction.
-  const double tol = h->prec == GQT_FP64 ? 1e-10 : 1e-5;
-  k_norm_check_msd<<<1, 256, 0, st>>>(partial, nb, R, (const int*)T.d_seg_blk.p, h->nseg, tol, (int*)h->d_flag.p);
-  check_launch("k_norm_check_msd");
 }
 
 void gqt::launch_velocity(gqt_ham* h, const void* x, void* y, void* ycopy, int R, cudaStream_t st) {
@@ -592,6 +718,7 @@ gqt_status gqt_set_launch(gqt_ham* h, int threads, int blocks_per_sm) {
   h->threads = threads;
   h->blocks_per_sm = blocks_per_sm;
   h->tables.clear();
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
   h->graphs.clear();
   API_END
 }
@@ -649,10 +776,10 @@ gqt_status gqt_dos_moments(gqt_ham* h, const void* d_phi, int R, int M, double* 
   const size_t bytes = (size_t)h->nseg * R * M * sizeof(double);
   if (is_host_ptr(mu)) {
     DevBuf& out = h->ws(WS_MU, bytes);
-    launch_moments(h, d_phi, d_phi, R, M, out.p, 1, st);
+    launch_moments(h, d_phi, d_phi, R, M, out.p, 2, st);
     deliver(out.p, mu, bytes, st);
   } else {
-    launch_moments(h, d_phi, d_phi, R, M, mu, 1, st);
+    launch_moments(h, d_phi, d_phi, R, M, mu, 2, st);
   }
   return finish_call(h, st, "gqt_dos_moments");
   API_END
@@ -770,7 +897,7 @@ gqt_status gqt_msd_moments(gqt_ham* h, void* d_p, void* d_px, int R, const doubl
     const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
     const auto c = evolve_coefs(h->dE * dt[k], +1, np);
     launch_msd_step(h, d_p, d_px, R, c, st);
-    launch_moments(h, d_px, d_px, R, M, dmu + k * row, 1, st);
+    launch_moments(h, d_px, d_px, R, M, dmu + k * row, 2, st);
   }
   if (host && Nt > 0) deliver(dmu, mu, Nt * row * sizeof(double), st);
   return finish_call(h, st, "gqt_msd_moments");
@@ -831,3 +958,258 @@ gqt_status gqt_sigma_msd(const double* d_msd, const double* dt, int Nt, int NE, 
 }
 
 }  // extern "C"
+
+// ====================================================================== adjoint (K9)
+
+namespace {
+
+// Adds to (gdiag, gslot) the gradient of J = Re sum_{m<P} coef_m <lam|T_m(H~)|r>
+// and writes rbar = sum_m conj(coef_m) T_m lam (dJ = Re <rbar|dr>).  If lbar is
+// non-null it receives sum_m coef_m T_m r (FP64).  u_m = T_m r is recomputed
+// from checkpoint pairs (u_c, u_{c+1}) taken every `stride` orders.
+template <class HT>
+void poly_adjoint(gqt_ham* h, const HT& H, const void* r, const void* lam, const std::vector<double2>& coef,
+                  int stride, void* rbar, double2* lbar, double* gdiag, double2* gslot, cudaStream_t st) {
+  using Tr = EllTraits<HT>;
+  using V = typename Tr::V;
+  const int P = (int)coef.size();
+  const BlockTable& T = h->table(1);
+  const int nb = T.nblocks;
+  const int* blk = (const int*)T.d_blk.p;
+  const size_t vb = h->vec_bytes(1);
+  const int s = std::max(2, stride);
+  const int nck = (P + s - 1) / s;
+  char* ck = (char*)h->ws(WS_ADJ0, (size_t)2 * nck * vb).p;
+  char* seg = (char*)h->ws(WS_ADJ0 + 1, (size_t)s * vb).p;
+  V* WA = (V*)h->ws(WS_ADJ0 + 2, vb).p;
+  V* WB = (V*)h->ws(WS_ADJ0 + 3, vb).p;
+  auto ckp = [&](int j, int q) { return (V*)(ck + ((size_t)2 * j + q) * vb); };
+  const double2 z = make_double2(0.0, 0.0);
+  const int thr = h->threads;
+  // forward pass: checkpoints (and lbar)
+  check_cuda(cudaMemcpyAsync(ckp(0, 0), r, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+  if (P > 1) {
+    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], coef[1], 1);
+    check_launch("k_recur(first)");
+    if (1 % s == 1) check_cuda(cudaMemcpyAsync(ckp(0, 1), WA, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+  } else if (lbar) {
+    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], z, 1);
+    check_launch("k_recur(first)");
+  }
+  const V* um2 = (const V*)r;
+  V* um1 = WA;
+  for (int m = 2; m < P; ++m) {
+    V* out = (m == 2) ? WB : const_cast<V*>(um2);
+    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, um1, um2, out, lbar, z, coef[m], 0);
+    check_launch("k_recur");
+    if (m % s == 0) check_cuda(cudaMemcpyAsync(ckp(m / s, 0), out, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    if (m % s == 1) check_cuda(cudaMemcpyAsync(ckp(m / s, 1), out, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    um2 = um1;
+    um1 = out;
+  }
+  // backward pass
+  check_cuda(cudaMemsetAsync(WA, 0, vb, st), "memset");
+  check_cuda(cudaMemsetAsync(WB, 0, vb, st), "memset");
+  V* X = WA;  // w_{m+1}
+  V* Y = WB;  // w_{m+2} -> w_m
+  for (int j = nck - 1; j >= 0; --j) {
+    const int c = j * s;
+    const int len = std::min(s, P - c);
+    std::vector<const V*> useg(len);
+    for (int q = 0; q < len; ++q) {
+      if (q < 2) {
+        useg[q] = ckp(j, q);
+      } else {
+        V* o = (V*)(seg + (size_t)q * vb);
+        k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, useg[q - 1], useg[q - 2], o, nullptr, z, z, 0);
+        check_launch("k_recur(segment)");
+        useg[q] = o;
+      }
+    }
+    for (int m = std::min(c + len, P - 1); m >= c + 1; --m) {
+      const double2 lc = make_double2(coef[m].x, -coef[m].y);
+      const double f = (m == 1 ? 1.0 : 2.0) / h->dE;
+      k_adj_step<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, X, Y, (const V*)lam, lc, useg[m - 1 - c], f, gdiag,
+                                                         gslot);
+      check_launch("k_adj_step");
+      std::swap(X, Y);
+    }
+  }
+  const double2 lc0 = make_double2(coef[0].x, -coef[0].y);
+  k_adj_final<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, P > 1 ? X : nullptr, Y, (const V*)lam, lc0, (V*)rbar);
+  check_launch("k_adj_final");
+}
+
+}  // namespace
+
+extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const double* dt, const int* Np, int Nt,
+                                        int M, const double* beta, int stride, double* loss, double* d_g_onsite,
+                                        double* d_g_slot, void* stream) {
+  API_BEGIN
+  check_common(h, 1);
+  require(d_phi && dt && beta && loss && d_g_onsite && d_g_slot && Nt >= 1 && M >= 1, "gqt_vac_loss_grad: bad argument");
+  require(h->nseg == 1, "gqt_vac_loss_grad: single-segment handles only");
+  cudaStream_t st = (cudaStream_t)stream;
+  reset_flag(h, st);
+  const int64_t n = h->n;
+  const int K = h->K;
+  const size_t vb = h->vec_bytes(1);
+  const BlockTable& T = h->table(1);
+  const int nb = T.nblocks;
+  const int* blk = (const int*)T.d_blk.p;
+  const int thr = h->threads;
+  if (stride <= 0) stride = (int)std::ceil(std::sqrt((double)M));
+  char* A = (char*)h->ws(WS_ADJ0 + 4, (size_t)Nt * vb).p;
+  char* B = (char*)h->ws(WS_ADJ0 + 5, (size_t)Nt * vb).p;
+  double* gdiag = (double*)h->ws(WS_ADJ0 + 6, (size_t)n * sizeof(double)).p;
+  double2* gslot = (double2*)h->ws(WS_ADJ0 + 7, (size_t)n * K * sizeof(double2)).p;
+  void* abar = h->ws(WS_ADJ0 + 8, vb).p;
+  void* bbar = h->ws(WS_ADJ0 + 9, vb).p;
+  double2* LB = (double2*)h->ws(WS_ADJ0 + 10, (size_t)n * sizeof(double2)).p;
+  void* tmp = h->ws(WS_ADJ0 + 11, vb).p;
+  void* l = h->ws(WS_L, vb).p;
+  double* dpart = (double*)h->ws(WS_ADJ0 + 12, (size_t)nb * sizeof(double)).p;
+  auto Ak = [&](int k) { return (void*)(A + (size_t)k * vb); };
+  auto Bk = [&](int k) { return (void*)(B + (size_t)k * vb); };
+  // forward states a_k = U(-t_k) phi, b_k = U(-t_k) V phi
+  launch_velocity(h, d_phi, Bk(0), Ak(0), 1, st);
+  std::vector<int> nps(Nt);
+  for (int k = 0; k < Nt; ++k) nps[k] = resolve_np(h, dt[k], Np ? Np[k] : 0);
+  for (int k = 0; k + 1 < Nt; ++k) {
+    check_cuda(cudaMemcpyAsync(Ak(k + 1), Ak(k), vb, cudaMemcpyDeviceToDevice, st), "copy");
+    check_cuda(cudaMemcpyAsync(Bk(k + 1), Bk(k), vb, cudaMemcpyDeviceToDevice, st), "copy");
+    void* sets[2] = {Ak(k + 1), Bk(k + 1)};
+    launch_evolve_sets<2>(h, sets, 1, evolve_coefs(h->dE * dt[k], -1, nps[k]), st, nullptr);
+  }
+  check_cuda(cudaMemsetAsync(gdiag, 0, (size_t)n * sizeof(double), st), "memset");
+  check_cuda(cudaMemsetAsync(gslot, 0, (size_t)n * K * sizeof(double2), st), "memset");
+  check_cuda(cudaMemsetAsync(abar, 0, vb, st), "memset");
+  check_cuda(cudaMemsetAsync(bbar, 0, vb, st), "memset");
+  std::vector<double> hpart(nb);
+  double total = 0.0;
+  dispatch(h, [&](auto H) {
+    using Tr = EllTraits<decltype(H)>;
+    using V = typename Tr::V;
+    for (int k = Nt - 1; k >= 0; --k) {
+      if (k + 1 < Nt) {
+        const auto c = evolve_coefs(h->dE * dt[k], -1, nps[k]);
+        poly_adjoint(h, H, Ak(k), abar, c, std::max(2, (int)std::ceil(std::sqrt((double)c.size()))), tmp, nullptr,
+                     gdiag, gslot, st);
+        std::swap(abar, tmp);
+        poly_adjoint(h, H, Bk(k), bbar, c, std::max(2, (int)std::ceil(std::sqrt((double)c.size()))), tmp, nullptr,
+                     gdiag, gslot, st);
+        std::swap(bbar, tmp);
+      }
+      launch_velocity(h, Ak(k), l, nullptr, 1, st);
+      std::vector<double2> bc(M);
+      for (int m = 0; m < M; ++m) bc[m] = make_double2(beta[(size_t)k * M + m], 0.0);
+      poly_adjoint(h, H, Bk(k), l, bc, stride, tmp, LB, gdiag, gslot, st);
+      k_axpy<V><<<nb, thr, 0, st>>>(blk, (V*)bbar, (const V*)tmp);
+      check_launch("k_axpy");
+      k_dot_re<V><<<nb, thr, 0, st>>>(blk, (const V*)l, LB, dpart);
+      check_launch("k_dot_re");
+      check_cuda(cudaMemcpyAsync(hpart.data(), dpart, nb * sizeof(double), cudaMemcpyDeviceToHost, st), "loss");
+      check_cuda(cudaStreamSynchronize(st), "loss");
+      for (int b = 0; b < nb; ++b) total += hpart[b];
+      k_vel_adj<Tr::fp64, Tr::ch, double2><<<nb, thr, 0, st>>>(H, blk, LB, (const V*)Ak(k), gslot);
+      check_launch("k_vel_adj");
+      k_vel_acc<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, 0.5 * h->dE, LB, (V*)abar);
+      check_launch("k_vel_acc");
+    }
+    k_vel_adj<Tr::fp64, Tr::ch, V><<<nb, thr, 0, st>>>(H, blk, (const V*)bbar, (const V*)d_phi, gslot);
+    check_launch("k_vel_adj");
+  });
+  const size_t tot = (size_t)n * K;
+  k_grad_out<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>((int)n, K, gslot, gdiag,
+                                                                            (double2*)d_g_slot, d_g_onsite);
+  check_launch("k_grad_out");
+  *loss = total;
+  return finish_call(h, st, "gqt_vac_loss_grad");
+  API_END
+}
+
+extern "C" gqt_status gqt_kpm_weights(int M, const double* d_E, int NE, const double* d_w, double energy_scale,
+                                      double n_over_omega, int kernel, double* d_beta, void* stream) {
+  API_BEGIN
+  require(d_E && d_w && d_beta && M >= 1 && NE >= 0 && energy_scale > 0 && (kernel == 0 || kernel == 1),
+          "gqt_kpm_weights: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* tab = nullptr;
+  check_cuda(cudaMallocAsync((void**)&tab, std::max<size_t>(1, (size_t)M * NE) * sizeof(double), st),
+             "cudaMallocAsync");
+  const size_t total = (size_t)M * NE;
+  if (total) {
+    k_kpm_table<<<(int)std::min<size_t>((total + 255) / 256, 8192), 256, 0, st>>>(M, d_E, NE, energy_scale,
+                                                                                   n_over_omega, kernel == 0, tab);
+    check_launch("k_kpm_table");
+  }
+  k_kpm_weights<<<(M + 127) / 128, 128, 0, st>>>(tab, M, NE, d_w, d_beta);
+  check_launch("k_kpm_weights");
+  check_cuda(cudaFreeAsync(tab, st), "cudaFreeAsync");
+  check_cuda(cudaStreamSynchronize(st), "gqt_kpm_weights");
+  API_END
+}
+
+// Autotuner: times the fused moment kernel (Re <l|T_m|r> orders, the VAC inner
+// loop) on zero-filled scratch vectors of the handle for each launch shape and
+// keeps the fastest.  Candidates: threads per CTA x CTAs per SM.
+extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_per_sm, void* stream) {
+  API_BEGIN
+  check_common(h, R);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vb = h->vec_bytes(R);
+  void* x = h->ws(WS_P, vb).p;
+  void* l = h->ws(WS_L, vb).p;
+  check_cuda(cudaMemsetAsync(x, 0, vb, st), "memset");
+  check_cuda(cudaMemsetAsync(l, 0, vb, st), "memset");
+  const int cand_t[] = {128, 256, 512};
+  const int cand_b[] = {2, 4, 8};
+  const int M = 12;
+  DevBuf scratch_mu;
+  scratch_mu.ensure((size_t)h->nseg * R * M * sizeof(double));
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  const bool graphs = h->use_graphs;
+  h->use_graphs = false;
+  float best = 1e30f;
+  int bt = h->threads, bb = h->blocks_per_sm;
+  try {
+    for (int t : cand_t)
+      for (int b : cand_b) {
+        h->threads = t;
+        h->blocks_per_sm = b;
+        h->tables.clear();
+        launch_moments(h, l, x, R, 4, scratch_mu.p, 1, st);  // warm-up (also builds the table)
+        check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
+        launch_moments(h, l, x, R, M, scratch_mu.p, 1, st);
+        check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
+        check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (ms < best) {
+          best = ms;
+          bt = t;
+          bb = b;
+        }
+      }
+  } catch (...) {
+    h->use_graphs = graphs;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->use_graphs = graphs;
+  h->threads = bt;
+  h->blocks_per_sm = bb;
+  h->tables.clear();
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  reset_flag(h, st);
+  check_cuda(cudaStreamSynchronize(st), "gqt_autotune");
+  if (threads) *threads = bt;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  API_END
+}

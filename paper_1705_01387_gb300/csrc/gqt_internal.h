@@ -83,6 +83,8 @@ struct gqt_ham {
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;
+  cudaStream_t gstream = nullptr;  // capture/replay stream of the graphs
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 
   const gqt::BlockTable& table(int R);
   gqt::DevBuf& ws(int slot, size_t bytes);
@@ -91,6 +93,6 @@ struct gqt_ham {
 };
 
 namespace gqt {
-void launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int mode, cudaStream_t st);
+void launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int kind, cudaStream_t st);
 void launch_velocity(gqt_ham* h, const void* x, void* y, void* ycopy, int R, cudaStream_t st);
 }  // namespace gqt

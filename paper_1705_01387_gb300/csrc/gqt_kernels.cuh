@@ -136,6 +136,10 @@ struct DotAcc<double2> {
     s.x = fma(t.x, t.x, s.x);
     s.x = fma(t.y, t.y, s.x);
   }
+  __device__ __forceinline__ void add_re(double2 l, double2 t) {  // Re conj(l) t into .x
+    s.x = fma(l.x, t.x, s.x);
+    s.x = fma(l.y, t.y, s.x);
+  }
   __device__ __forceinline__ double2 get() { return s; }
 };
 
@@ -179,6 +183,11 @@ struct DotAcc<float2> {
   __device__ __forceinline__ void add_norm(float2 t) {
     re.add_prod(t.x, t.x);
     re.add_prod(t.y, t.y);
+    if (++cnt == 16) flush();
+  }
+  __device__ __forceinline__ void add_re(float2 l, float2 t) {
+    re.add_prod(l.x, t.x);
+    re.add_prod(l.y, t.y);
     if (++cnt == 16) flush();
   }
   __device__ __forceinline__ double2 get() {
@@ -503,6 +512,130 @@ __global__ void k_msd_evolve(Ell<FP64, CH> H, const int* __restrict__ blk, int R
   }
 }
 
+// Real-part moments Re <l|T_m|r> (the VAC row of Eq. 29 keeps only the real
+// part): same recursion as k_cheb with half the dot-product work.  Slots as k_cheb.
+template <bool FP64, bool CH>
+__global__ void k_cheb_re(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs,
+                          const typename Prec<FP64>::V* __restrict__ tm1, const typename Prec<FP64>::V* tm2,
+                          typename Prec<FP64>::V* tout, const typename Prec<FP64>::V* __restrict__ l,
+                          double2* __restrict__ partial, int nblocks, int slot0, int slot_norm, int first) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  if (first) {
+    DotAcc<V> d0, d1, nl, nr;
+    for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+      const int i = (int)(e >> rs);
+      const V lv = __ldg(l + e);
+      V zero;
+      zero.x = 0;
+      zero.y = 0;
+      V y = cscale(apply2h<FP64, CH>(H, tm1, i, r, rs, zero), (S)0.5);
+      tout[e] = y;
+      const V t0 = __ldg(tm1 + e);
+      d0.add_re(lv, t0);
+      d1.add_re(lv, y);
+      nl.add_norm(lv);
+      nr.add_norm(t0);
+    }
+    double2 v[3] = {d0.get(), d1.get(), make_double2(nl.get().x, nr.get().x)};
+    block_reduce_r<3>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(slot0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+      partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
+    }
+  } else {
+    DotAcc<V> d1;
+    for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+      const int i = (int)(e >> rs);
+      V y = apply2h<FP64, CH>(H, tm1, i, r, rs, cneg(tm2[e]));
+      tout[e] = y;
+      d1.add_re(__ldg(l + e), y);
+    }
+    double2 v[1] = {d1.get()};
+    block_reduce_r<1>(v, R, smem);
+    if ((int)threadIdx.x < R) partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+  }
+}
+
+// Moments of l = r = phi by the product identities of Chebyshev polynomials,
+// T_{2n} = 2 T_n T_n - T_0 and T_{2n+1} = 2 T_{n+1} T_n - T_1, so that
+// mu_{2n} = 2 <u_n|u_n> - mu_0 and mu_{2n+1} = 2 <u_{n+1}|u_n> - mu_1 with
+// u_n = T_n(H~) phi: M moments from ceil(M/2) recursion steps (kernel polynomial
+// method, Weisse et al., Rev. Mod. Phys. 78, 275 (2006), Sec. II.C).  Both inner
+// products are real for Hermitian H~.
+// first != 0: tout = u_1 = H~ u_0 (tm1 = u_0); raw sums s_0 = <u_0|u_0>, s_1 = <u_1|u_0>
+// into slots 0, 1.  Otherwise (step m >= 2, tm1 = u_{m-1}, tm2 = u_{m-2}): tout = u_m,
+// s_{2m-2} = <u_{m-1}|u_{m-1}> and s_{2m-1} = <u_m|u_{m-1}> into slots 2m-2, 2m-1.
+template <bool FP64, bool CH>
+__global__ void k_cheb_dbl(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int rs,
+                           const typename Prec<FP64>::V* __restrict__ tm1, const typename Prec<FP64>::V* tm2,
+                           typename Prec<FP64>::V* tout, double2* __restrict__ partial, int nblocks, int m) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  const size_t beg = (size_t)blk[b] << rs, end = (size_t)blk[b + 1] << rs;
+  const int r = threadIdx.x & (R - 1);
+  DotAcc<V> a0, a1;
+  for (size_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = (int)(e >> rs);
+    const V own = __ldg(tm1 + e);
+    V acc;
+    if (m == 1) {
+      acc.x = 0;
+      acc.y = 0;
+    } else {
+      acc = cneg(tm2[e]);
+    }
+    acc = cmul_acc(acc, __ldg(H.diag2 + i), own);
+    for (int k = 0; k < H.K; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      const int j = __ldg(H.idx + s);
+      acc = cmul_acc(acc, __ldg(H.hop2 + s), __ldg(tm1 + (((size_t)j << rs) + r)));
+    }
+    if (m == 1) acc = cscale(acc, (S)0.5);
+    tout[e] = acc;
+    a0.add_norm(own);
+    a1.add_re(acc, own);
+  }
+  double2 v[2] = {a0.get(), a1.get()};
+  block_reduce_r<2>(v, R, smem);
+  if ((int)threadIdx.x < R) {
+    const int k0 = 2 * m - 2;
+    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
+    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+  }
+}
+
+// Second pass of k_cheb_dbl: mu[s][r][k] = s_k for k < 2, 2 s_k - s_{k mod 2} otherwise,
+// each s summed over the segment's CTAs in CTA order.  Bound |mu_k| <= (1+tol) mu_0.
+__global__ void k_reduce_dbl(const double2* __restrict__ partial, int M, int nblocks, int R,
+                             const int* __restrict__ seg_blk, int nseg, double bound_factor, double* __restrict__ out,
+                             int* __restrict__ flag) {
+  const size_t total = (size_t)nseg * R * M;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % R);
+    const int k = (int)((t / R) % M);
+    const int s = (int)(t / ((size_t)R * M));
+    double sk = 0.0, s0 = 0.0, sp = 0.0;
+    const int kp = k & 1;
+    for (int b = seg_blk[s]; b < seg_blk[s + 1]; ++b) {
+      sk += partial[((size_t)k * nblocks + b) * R + r].x;
+      s0 += partial[((size_t)0 * nblocks + b) * R + r].x;
+      sp += partial[((size_t)kp * nblocks + b) * R + r].x;
+    }
+    const double mu = (k < 2) ? sk : 2.0 * sk - sp;
+    out[((size_t)s * R + r) * M + k] = mu;
+    if (!isfinite(mu)) atomicOr(flag, 4);
+    if (fabs(mu) > s0 * bound_factor + 1e-300) atomicOr(flag, 2);
+  }
+}
+
 // Norm check of an evolution: slots q (before) and NSET + q (after) hold the
 // partial squared norms of set q.  | |after| - |before| | > tol |before| sets
 // bit 3 of *flag.  norms (optional) receives [nseg][R][NSET][2] squared norms.
@@ -671,4 +804,209 @@ __global__ void k_random_phase(int n, int R, const uint64_t* __restrict__ keys, 
   }
 }
 
+}  // namespace gqt
+
+namespace gqt {
+
+// ------------------------------------------------------------ K9: adjoint
+//
+// Reverse-mode derivative of J = Re sum_{m<P} coef_m <lam| T_m(H~) |r> with
+// u_m = T_m r (not in the paper; it differentiates Eqs. 17, 21 and 29).  The
+// adjoint vectors obey the transposed recurrence
+//   w_m = conj(coef_m) lam + 2 H~ w_{m+1} - w_{m+2},   w_P = w_{P+1} = 0,
+// and dJ = Re sum_ij conj(G_ij) dH~_ij with G = w_1 u_0^+ + 2 sum_{m>=2} w_m u_{m-1}^+,
+// needed only on the diagonal and the ELL slots.
+
+// Plain recurrence step: out = 2H~ t1 - t2 (first: out = H~ t1); if acc != null,
+// first: acc = cA t1 + cB out, else acc += cB out.
+template <bool FP64, bool CH>
+__global__ void k_recur(Ell<FP64, CH> H, const int* __restrict__ blk, const typename Prec<FP64>::V* __restrict__ t1,
+                        const typename Prec<FP64>::V* t2, typename Prec<FP64>::V* out, double2* __restrict__ acc,
+                        double2 cA, double2 cB, int first) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    V y;
+    if (first) {
+      V zero;
+      zero.x = 0;
+      zero.y = 0;
+      y = cscale(apply2h<FP64, CH>(H, t1, i, 0, 0, zero), (S)0.5);
+    } else {
+      y = apply2h<FP64, CH>(H, t1, i, 0, 0, cneg(t2[i]));
+    }
+    out[i] = y;
+    if (acc) {
+      if (first)
+        acc[i] = cfma_d(cfma_d(make_double2(0.0, 0.0), cA, __ldg(t1 + i)), cB, y);
+      else
+        acc[i] = cfma_d(acc[i], cB, y);
+    }
+  }
+}
+
+// One adjoint order m: w_m = lc lam + 2H~ w1 - w2 (w1 = w_{m+1}, w2 = w_{m+2},
+// w_m overwrites w2) and G += f w_m conj(u_{m-1}) on the diagonal (gdiag, real
+// part) and on the slots (gslot [K][n]).  f = (m == 1 ? 1 : 2) / dE.
+template <bool FP64, bool CH>
+__global__ void k_adj_step(Ell<FP64, CH> H, const int* __restrict__ blk, const typename Prec<FP64>::V* __restrict__ w1,
+                           typename Prec<FP64>::V* w2, const typename Prec<FP64>::V* __restrict__ lam, double2 lc,
+                           const typename Prec<FP64>::V* __restrict__ u, double f, double* __restrict__ gdiag,
+                           double2* __restrict__ gslot) {
+  using V = typename Prec<FP64>::V;
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    V y = apply2h<FP64, CH>(H, w1, i, 0, 0, cneg(w2[i]));
+    double2 wd = cfma_d(to_d2(y), lc, __ldg(lam + i));
+    const V w = from_d2<V>(wd);
+    w2[i] = w;
+    wd = to_d2(w);
+    const double2 ui = to_d2(__ldg(u + i));
+    gdiag[i] += f * (wd.x * ui.x + wd.y * ui.y);
+    for (int k = 0; k < H.K; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      const double2 uj = to_d2(__ldg(u + __ldg(H.idx + s)));
+      double2 g = gslot[s];
+      // w * conj(uj)
+      g.x += f * (wd.x * uj.x + wd.y * uj.y);
+      g.y += f * (wd.y * uj.x - wd.x * uj.y);
+      gslot[s] = g;
+    }
+  }
+}
+
+// rbar = lc0 lam + H~ w1 - w2 (Clenshaw end, = sum_m conj(coef_m) T_m lam); w1 may be null (P = 1).
+template <bool FP64, bool CH>
+__global__ void k_adj_final(Ell<FP64, CH> H, const int* __restrict__ blk, const typename Prec<FP64>::V* __restrict__ w1,
+                            const typename Prec<FP64>::V* __restrict__ w2, const typename Prec<FP64>::V* __restrict__ lam,
+                            double2 lc0, typename Prec<FP64>::V* __restrict__ rbar) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    double2 acc = cfma_d(make_double2(0.0, 0.0), lc0, __ldg(lam + i));
+    if (w1) {
+      V zero;
+      zero.x = 0;
+      zero.y = 0;
+      V y = cscale(apply2h<FP64, CH>(H, w1, i, 0, 0, zero), (S)0.5);
+      const double2 yd = to_d2(y), w2d = to_d2(__ldg(w2 + i));
+      acc.x += yd.x - w2d.x;
+      acc.y += yd.y - w2d.y;
+    }
+    rbar[i] = from_d2<V>(acc);
+  }
+}
+
+__device__ __forceinline__ double2 hop_d(double2 h) { return h; }
+__device__ __forceinline__ double2 hop_d(float2 h) { return to_d2(h); }
+__device__ __forceinline__ double hop_d(double h) { return h; }
+__device__ __forceinline__ double hop_d(float h) { return (double)h; }
+
+// Velocity part of the gradient: l = V x with V_ij = i dx_ij H_ij (unscaled H), so
+// G_ij += lbar_i (-i dx_ij) conj(x_j) (slots only; V has no diagonal).
+template <bool FP64, bool CH, class LB>
+__global__ void k_vel_adj(Ell<FP64, CH> H, const int* __restrict__ blk, const LB* __restrict__ lbar,
+                          const typename Prec<FP64>::V* __restrict__ x, double2* __restrict__ gslot) {
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    const double2 lb = to_d2(lbar[i]);
+    for (int k = 0; k < H.K; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      const double2 xj = to_d2(__ldg(x + __ldg(H.idx + s)));
+      const double d = (double)__ldg(H.dx + s);
+      // lbar * (-i d) * conj(xj) = -i d (lb.x + i lb.y)(xj.x - i xj.y)
+      const double re = lb.x * xj.x + lb.y * xj.y, im = lb.y * xj.x - lb.x * xj.y;
+      double2 g = gslot[s];
+      g.x += d * im;
+      g.y += -d * re;
+      gslot[s] = g;
+    }
+  }
+}
+
+// y += V x for a double2 accumulator y (x storage precision), V = i dE sum dx H~.
+template <bool FP64, bool CH>
+__global__ void k_vel_acc(Ell<FP64, CH> H, const int* __restrict__ blk, double half_dE,
+                          const double2* __restrict__ x, typename Prec<FP64>::V* __restrict__ y) {
+  using V = typename Prec<FP64>::V;
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int k = 0; k < H.K; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      const int j = __ldg(H.idx + s);
+      const double d = (double)__ldg(H.dx + s);
+      a = cmul_acc(a, hop_d(__ldg(H.hop2 + s)), cscale(x[j], d));
+    }
+    double2 yo = to_d2(y[i]);
+    yo.x += -a.y * half_dE;
+    yo.y += a.x * half_dE;
+    y[i] = from_d2<V>(yo);
+  }
+}
+
+// Re <l|x> partial sums per CTA (x double2).
+template <class V>
+__global__ void k_dot_re(const int* __restrict__ blk, const V* __restrict__ l, const double2* __restrict__ x,
+                         double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    const double2 lv = to_d2(l[i]);
+    const double2 xv = x[i];
+    s += lv.x * xv.x + lv.y * xv.y;
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    partial[b] = t;
+  }
+}
+
+// y += x (storage precision).
+template <class V>
+__global__ void k_axpy(const int* __restrict__ blk, V* __restrict__ y, const V* __restrict__ x) {
+  const int b = blockIdx.x;
+  for (int i = blk[b] + threadIdx.x; i < blk[b + 1]; i += blockDim.x) {
+    V a = y[i];
+    const V c = x[i];
+    a.x += c.x;
+    a.y += c.y;
+    y[i] = a;
+  }
+}
+
+// Slot-major [K][n] double2 -> row-major [n][K] double2; diagonal copied.
+__global__ void k_grad_out(int n, int K, const double2* __restrict__ gslot, const double* __restrict__ gdiag,
+                           double2* __restrict__ out_slot, double* __restrict__ out_diag) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * K; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / K), k = (int)(t % K);
+    out_slot[t] = gslot[(size_t)k * n + i];
+    if (k == 0) out_diag[i] = gdiag[i];
+  }
+}
+
+}  // namespace gqt
+
+namespace gqt {
+// beta[n] = sum_e w[e] tab[n][e]: the transpose of the reconstruction (the weight
+// each moment carries in a weighted sum of reconstructed values).  NaN entries of
+// the table (|E| >= dE) must carry zero weight and are skipped when w[e] == 0.
+__global__ void k_kpm_weights(const double* __restrict__ tab, int M, int NE, const double* __restrict__ w,
+                              double* __restrict__ beta) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = 0; e < NE; ++e) {
+      const double we = w[e];
+      if (we != 0.0) s += we * tab[(size_t)n * NE + e];
+    }
+    beta[n] = s;
+  }
+}
 }  // namespace gqt

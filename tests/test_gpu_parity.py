@@ -246,3 +246,39 @@ def test_non_hermitian_input_is_einval():
     with pytest.raises(g.GqtError) as e:
         g.gqt_build_hamiltonian(lat, 5.0)
     assert e.value.status == g.GQT_EINVAL
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5, 301])
+def test_dos_moment_counts_edge_cases(models, M):
+    """l = r moments use two moments per recursion step; odd and tiny M must still
+    give exactly M moments equal to the plain recursion's."""
+    lat, dE = models["square41x29"]
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    phi = S.random_phase(lat.n, 1, seed=31)
+    mu = np.full((1, 1, M), np.nan)
+    g.gqt_dos_moments(ham, dev(phi), 1, M, mu)
+    ref = O.Hamiltonian(lat, dE).dos_moments(phi[:, 0], M)
+    assert nerr(mu.reshape(M), ref) < TOL64
+
+
+def test_fp32_vac_msd_error_table(models):
+    """FP32 storage with FP64 accumulation on VAC and MSD rows: normalised error vs the
+    FP64 oracle below 1e-4 (stated bound for these lengths)."""
+    lat, dE = models["honeycomb32x32"]
+    ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP32_ACC64)
+    phi = S.random_phase(lat.n, 1, seed=41)
+    dts = np.full(3, 1 / 2.7)
+    Np = [O.np_rule(dE * d, 64) for d in dts]
+    M = 256
+    d = dev(phi, False)
+    a, b = torch.empty_like(d), torch.empty_like(d)
+    g.gqt_vac_init(ham, d, a, b, 1)
+    vac = np.empty((3, 1, 1, M))
+    g.gqt_vac_moments(ham, a, b, 1, dts, M, vac, Np=Np)
+    p, px = torch.empty_like(d), torch.empty_like(d)
+    g.gqt_msd_init(ham, d, p, px, 1)
+    msd = np.empty((3, 1, 1, M))
+    g.gqt_msd_moments(ham, p, px, 1, dts, M, msd, Np=Np)
+    h = O.Hamiltonian(lat, dE)
+    assert nerr(vac.reshape(3, M), h.vac_moments(phi[:, 0], dts, Np, M)) < 1e-4
+    assert nerr(msd.reshape(3, M), h.msd_moments(phi[:, 0], dts, Np, M)) < 1e-4

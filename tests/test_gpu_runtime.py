@@ -1,0 +1,166 @@
+"""Runtime features of the library on the GPU: CUDA-graph replay, the autotuner,
+launch-shape changes, resumable time loops and full-size sampled parity."""
+import numpy as np
+import pytest
+
+import gqt_synth as S
+import oracle as O
+
+torch = pytest.importorskip("torch")
+g = pytest.importorskip("paper_1705_01387_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def nerr(x, y):
+    return float(np.max(np.abs(np.asarray(x) - np.asarray(y))) / max(float(np.max(np.abs(y))), 1e-300))
+
+
+def _c1():
+    w = S.config(0)
+    return w, S.build_lattice(w.lattice_args, w.seed)
+
+
+def _vac(ham, phi, dts, M, Np):
+    a, b = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_vac_init(ham, phi, a, b, phi.shape[1])
+    out = np.empty((len(dts), ham.nseg, phi.shape[1], M))
+    g.gqt_vac_moments(ham, a, b, phi.shape[1], dts, M, out, Np=Np)
+    return out
+
+
+def test_graph_replay_is_bit_identical_to_direct_launches():
+    w, lat = _c1()
+    ham = g.gqt_build_hamiltonian(lat, w.energy_scale)
+    phi = torch.from_numpy(S.random_phase(lat.n, 1, seed=w.seed)).cuda()
+    dts = np.full(3, w.dt)
+    Np = [g.gqt_np_rule(w.energy_scale * d) for d in dts]
+    g.gqt_set_graphs(ham, True)
+    first = _vac(ham, phi, dts, 200, Np)
+    again = _vac(ham, phi, dts, 200, Np)  # replays the cached graphs
+    g.gqt_set_graphs(ham, False)
+    direct = _vac(ham, phi, dts, 200, Np)
+    assert np.array_equal(first, again) and np.array_equal(first, direct)
+
+
+def test_autotune_and_launch_shapes_keep_results():
+    lat = S.square(61, 47, -1.0, 4.0, seed=5)
+    dE = S.energy_scale_rule(4, -1.0, 4.0)
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    phi = S.random_phase(lat.n, 8, seed=6)
+    d = torch.from_numpy(phi).cuda()
+    ref = O.Hamiltonian(lat, dE).dos_moments(phi[:, 3], 128)
+    thr, bps = g.gqt_autotune(ham, 8)
+    assert thr in (128, 256, 512) and bps in (2, 4, 8)
+    for t, b in ((thr, bps), (128, 2), (512, 8), (256, 4)):
+        g.gqt_set_launch(ham, t, b)
+        mu = np.empty((1, 8, 128))
+        g.gqt_dos_moments(ham, d, 8, 128, mu)
+        assert nerr(mu[0, 3], ref) < 1e-10
+
+
+def test_time_loop_is_resumable():
+    """Nt steps in one call equal the same steps split over two calls (state in/out)."""
+    w, lat = _c1()
+    ham = g.gqt_build_hamiltonian(lat, w.energy_scale)
+    phi = torch.from_numpy(S.random_phase(lat.n, 1, seed=3)).cuda()
+    dts = np.array([0.3, 0.5, 0.2, 0.4])
+    Np = [g.gqt_np_rule(w.energy_scale * d) for d in dts]
+    whole = _vac(ham, phi, dts, 64, Np)
+    a, b = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_vac_init(ham, phi, a, b, 1)
+    p1 = np.empty((2, 1, 1, 64))
+    p2 = np.empty((2, 1, 1, 64))
+    g.gqt_vac_moments(ham, a, b, 1, dts[:2], 64, p1, Np=Np[:2])
+    g.gqt_vac_moments(ham, a, b, 1, dts[2:], 64, p2, Np=Np[2:])
+    assert nerr(np.concatenate([p1, p2]), whole) < 1e-13
+    p, px = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_msd_init(ham, phi, p, px, 1)
+    m_all = np.empty((4, 1, 1, 64))
+    g.gqt_msd_moments(ham, p, px, 1, dts, 64, m_all, Np=Np)
+    g.gqt_msd_init(ham, phi, p, px, 1)
+    m1 = np.empty((2, 1, 1, 64))
+    m2 = np.empty((2, 1, 1, 64))
+    g.gqt_msd_moments(ham, p, px, 1, dts[:2], 64, m1, Np=Np[:2])
+    g.gqt_msd_moments(ham, p, px, 1, dts[2:], 64, m2, Np=Np[2:])
+    assert nerr(np.concatenate([m1, m2]), m_all) < 1e-13
+
+
+def _ball(lat, centre, radius):
+    """Sites within `radius` hops of `centre` and the induced model (same H entries)."""
+    dist = {centre: 0}
+    frontier = [centre]
+    for d in range(radius):
+        nxt = []
+        for i in frontier:
+            for k in range(lat.nb_count[i]):
+                j = int(lat.nb_idx[i, k])
+                if j not in dist:
+                    dist[j] = d + 1
+                    nxt.append(j)
+        frontier = nxt
+    sites = np.array(sorted(dist))
+    pos = {s: q for q, s in enumerate(sites)}
+    n, K = sites.size, lat.max_nb
+    sub = S.Lattice("ball", n, K, np.zeros(n, np.int32), np.zeros((n, K), np.int32), np.zeros((n, K), np.complex128),
+                    lat.onsite[sites].copy(), np.zeros((n, K)), 0.0, 1.0)
+    for q, s in enumerate(sites):
+        c = 0
+        for k in range(lat.nb_count[s]):
+            j = int(lat.nb_idx[s, k])
+            if j in pos:
+                sub.nb_idx[q, c] = pos[j]
+                sub.hop[q, c] = lat.hop[s, k]
+                sub.dx[q, c] = lat.dx[s, k]
+                c += 1
+        sub.nb_count[q] = c
+        sub.nb_idx[q, c:] = q
+    return sub, pos[centre]
+
+
+@pytest.mark.slow
+def test_full_size_sampled_local_moments():
+    """Honeycomb 4096 x 2048 (N = 16,777,216), FP64, the benchmark's launch shape:
+    local moments <e_i|T_m(H~)|e_i> for sampled sites i, m < 40, equal the oracle's on
+    the ball of radius 20 around i (closed walks of length m stay within m/2 hops)."""
+    w = S.config(1)
+    lat = S.build_lattice(w.lattice_args, w.seed)
+    dE = w.energy_scale
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    M = 40
+    rng = np.random.default_rng(5)
+    for i in rng.choice(lat.n, 3, replace=False):
+        e = torch.zeros((lat.n, 1), dtype=torch.complex128, device="cuda")
+        e[int(i), 0] = 1.0
+        mu = np.empty((1, 1, M))
+        g.gqt_dos_moments(ham, e, 1, M, mu)
+        sub, c = _ball(lat, int(i), 20)
+        ec = np.zeros(sub.n, np.complex128)
+        ec[c] = 1.0
+        ref = O.Hamiltonian(sub, dE).dos_moments(ec, M)
+        assert nerr(mu.reshape(M), ref) < 1e-10
+    # properties at full size: unit norm moments bounded, evolution unitary and reversible
+    phi = torch.empty((lat.n, 1), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, w.seed, 1, phi)
+    mu = np.empty((1, 1, 200))
+    g.gqt_dos_moments(ham, phi, 1, 200, mu)
+    assert abs(mu[0, 0, 0] - 1.0) < 1e-12 and np.all(np.abs(mu) <= 1 + 1e-9)
+    psi = phi.clone()
+    nrm = np.empty(1)
+    g.gqt_evolve(ham, psi, 1, w.dt, 1, 0, norm=nrm)
+    g.gqt_evolve(ham, psi, 1, w.dt, -1, 0, norm=nrm)
+    assert abs(nrm[0] - 1.0) < 1e-12
+    assert float((psi - phi).abs().max()) < 1e-13
+
+
+def test_forward_then_backward_evolution_on_one_handle():
+    """U(-dt) U(+dt) phi = phi with both calls on one handle (distinct cached graphs)."""
+    lat = S.honeycomb(40, 30, -2.7, 2.0, seed=8)
+    dE = S.energy_scale_rule(3, -2.7, 2.0)
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    phi = torch.from_numpy(S.random_phase(lat.n, 2, seed=9)).cuda()
+    psi = phi.clone()
+    for _ in range(2):  # the second round replays both graphs
+        g.gqt_evolve(ham, psi, 2, 0.74, 1)
+        g.gqt_evolve(ham, psi, 2, 0.74, -1)
+    assert float((psi - phi).abs().max()) < 1e-13
