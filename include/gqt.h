@@ -215,10 +215,18 @@ gqt_status gqt_bessel(double x, int count, double* J);
 int gqt_np_rule(double x, int cap);
 
 /* Kernel launch shape for a handle: threads per block and blocks per SM of the
- * Chebyshev kernels (0 = library default).  gqt_autotune times the candidates
- * on a scratch copy of one Chebyshev step for the given R and keeps the fastest. */
+ * Chebyshev kernels (0 = library default).  gqt_autotune times every variant x
+ * threads x blocks-per-SM candidate on zero-filled scratch vectors (a few
+ * Re <l|T_m|r> orders for the given R) and keeps the fastest. */
 gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
-gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, void* stream);
+/* Moment-kernel variant: 0 = each CTA walks one contiguous chunk of sites; 1 =
+ * wavefront order (the CTAs of a segment stride through it together, so
+ * neighbour gathers hit in L2); 2 = wavefront with two elements in flight per
+ * thread.  Variants 1-2 cover 2, 3, 4 or 6 neighbour slots and up to 256
+ * threads per CTA; otherwise variant 0 runs.  Default 2.  gqt_autotune also
+ * chooses the variant. */
+gqt_status gqt_set_variant(gqt_ham* ham, int variant);
+gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, int* variant, void* stream);
 
 /* Use CUDA graphs for repeated loops (default 1). */
 gqt_status gqt_set_graphs(gqt_ham* ham, int enable);

@@ -61,8 +61,9 @@ _SIGS = {
     "gqt_bessel": [_D, _I, _P],
     "gqt_np_rule": [_D, _I],
     "gqt_set_launch": [_P, _I, _I],
-    "gqt_autotune": [_P, _I, _P, _P, _P],
+    "gqt_autotune": [_P, _I, _P, _P, _P, _P],
     "gqt_set_graphs": [_P, _I],
+    "gqt_set_variant": [_P, _I],
     "gqt_launch_count": [],
     "gqt_profile_start": [],
     "gqt_profile_stop": [_P, _P, _I],
@@ -338,10 +339,15 @@ def gqt_set_launch(ham: Ham, threads: int = 0, blocks_per_sm: int = 0):
     _check(lib().gqt_set_launch(ham.ptr, int(threads), int(blocks_per_sm)))
 
 
+def gqt_set_variant(ham: Ham, variant: int):
+    _check(lib().gqt_set_variant(ham.ptr, int(variant)))
+
+
 def gqt_autotune(ham: Ham, R: int, stream=None):
-    thr, bps = C.c_int(), C.c_int()
-    _check(lib().gqt_autotune(ham.ptr, int(R), C.byref(thr), C.byref(bps), _stream(stream)))
-    return thr.value, bps.value
+    """Returns (threads, blocks_per_sm, variant) chosen and set on the handle."""
+    thr, bps, var = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().gqt_autotune(ham.ptr, int(R), C.byref(thr), C.byref(bps), C.byref(var), _stream(stream)))
+    return thr.value, bps.value, var.value
 
 
 def gqt_set_graphs(ham: Ham, enable: bool):

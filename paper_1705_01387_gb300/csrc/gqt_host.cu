@@ -274,6 +274,13 @@ const BlockTable& gqt_ham::table(int R) {
     seg_blk.push_back((int)blk.size() - 1);
   }
   t->nblocks = (int)blk.size() - 1;
+  std::vector<int4> tab4(t->nblocks);
+  for (int s = 0; s < nseg; ++s) {
+    const int G = seg_blk[s + 1] - seg_blk[s];
+    for (int q = 0; q < G; ++q) tab4[seg_blk[s] + q] = make_int4((int)seg[s], (int)seg[s + 1], q, G);
+  }
+  t->d_tab4.ensure(tab4.size() * sizeof(int4));
+  check_cuda(cudaMemcpy(t->d_tab4.p, tab4.data(), tab4.size() * sizeof(int4), cudaMemcpyHostToDevice), "table");
   t->d_blk.ensure(blk.size() * sizeof(int));
   t->d_seg_blk.ensure(seg_blk.size() * sizeof(int));
   check_cuda(cudaMemcpy(t->d_blk.p, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice), "table");
@@ -353,6 +360,57 @@ static void reset_flag(gqt_ham* h, cudaStream_t st) {
 
 // ====================================================================== moments core
 
+// Wavefront-ordered moment kernels for the common neighbour counts (2, 3, 4, 6
+// slots); other counts return false and use the chunk-ordered kernels.
+template <bool FP64, bool CH, class V>
+static bool launch_wave_re(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable& T, int R, int rs, const V* tm1,
+                           const V* tm2, V* tout, const V* l, double2* partial, int slot0, int slot_norm, int first,
+                           cudaStream_t st) {
+  if (h->threads > 256 || h->variant == 0) return false;
+  const int4* tab = (const int4*)T.d_tab4.p;
+  const size_t sm = smem_bytes(h, R, 3);
+#define GQT_WAVE_RE(KK)                                                                                          \
+  if (h->variant == 1)                                                                                           \
+    k_cheb_re_w<FP64, CH, 1, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, l, partial, \
+                                                                    T.nblocks, slot0, slot_norm, first);       \
+  else                                                                                                           \
+    k_cheb_re_w<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, l, partial, \
+                                                                    T.nblocks, slot0, slot_norm, first);       \
+  return true;
+  switch (H.K) {
+    case 2: GQT_WAVE_RE(2)
+    case 3: GQT_WAVE_RE(3)
+    case 4: GQT_WAVE_RE(4)
+    case 6: GQT_WAVE_RE(6)
+    default: return false;
+  }
+#undef GQT_WAVE_RE
+}
+
+template <bool FP64, bool CH, class V>
+static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable& T, int R, int rs, const V* tm1,
+                            const V* tm2, V* tout, double2* partial, int m, cudaStream_t st) {
+  if (h->threads > 256 || h->variant == 0) return false;
+  const int4* tab = (const int4*)T.d_tab4.p;
+  const size_t sm = smem_bytes(h, R, 3);
+#define GQT_WAVE_DBL(KK)                                                                                           \
+  if (h->variant == 1)                                                                                             \
+    k_cheb_dbl_w<FP64, CH, 1, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, partial,     \
+                                                                     T.nblocks, m);                               \
+  else                                                                                                             \
+    k_cheb_dbl_w<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, partial,     \
+                                                                     T.nblocks, m);                               \
+  return true;
+  switch (H.K) {
+    case 2: GQT_WAVE_DBL(2)
+    case 3: GQT_WAVE_DBL(3)
+    case 4: GQT_WAVE_DBL(4)
+    case 6: GQT_WAVE_DBL(6)
+    default: return false;
+  }
+#undef GQT_WAVE_DBL
+}
+
 // Launch the moment recursion of r against l and reduce into out, layout
 // [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
 // (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
@@ -372,7 +430,8 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
   const size_t total = (size_t)h->nseg * R * M;
   const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
   const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p},
-                                 {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb});
+                                 {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb,
+                                  (double)h->variant});
   run_graph(h, key, st, [&](cudaStream_t s2) {
     dispatch(h, [&](auto H) {
       using Tr = EllTraits<decltype(H)>;
@@ -384,20 +443,16 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       const int* blk = (const int*)T.d_blk.p;
       if (kind == 2) {
         const int steps = (M + 1) / 2;  // step m yields moments 2m-2 and 2m-1
-        size_t pe = prof_begin(s2);
-        k_cheb_dbl<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1,
-                                                                                  partial, nb, 1);
-        check_launch("k_cheb_dbl(first)");
-        prof_end(pe, 0, s2);
-        for (int m = 2; m <= std::max(steps, 1); ++m) {
-          const V* tm1 = (m - 1) % 2 == 1 ? W1 : W2;
+        for (int m = 1; m <= std::max(steps, 1); ++m) {
+          const V* tm1 = (m == 1) ? rv : ((m - 1) % 2 == 1 ? W1 : W2);
           V* tout = (m % 2 == 1) ? W1 : W2;
-          const V* tm2 = (m == 2) ? rv : tout;
-          pe = prof_begin(s2);
-          k_cheb_dbl<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout,
-                                                                                    partial, nb, m);
+          const V* tm2 = (m == 1) ? nullptr : ((m == 2) ? rv : tout);
+          size_t pe = prof_begin(s2);
+          if (!launch_wave_dbl<Tr::fp64, Tr::ch>(h, H, T, R, rs, tm1, tm2, tout, partial, m, s2))
+            k_cheb_dbl<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout,
+                                                                                      partial, nb, m);
           check_launch("k_cheb_dbl");
-          prof_end(pe, 5, s2);
+          prof_end(pe, m == 1 ? 0 : 5, s2);
         }
         return;
       }
@@ -405,7 +460,7 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       if (kind == 0)
         k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1, lv,
                                                                               partial, nb, 0, slot_norm, 1);
-      else
+      else if (!launch_wave_re<Tr::fp64, Tr::ch>(h, H, T, R, rs, rv, (const V*)nullptr, W1, lv, partial, 0, slot_norm, 1, s2))
         k_cheb_re<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, rv, nullptr, W1, lv,
                                                                                  partial, nb, 0, slot_norm, 1);
       check_launch("k_cheb(first)");
@@ -418,7 +473,7 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
         if (kind == 0)
           k_cheb<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout, lv,
                                                                                 partial, nb, m, slot_norm, 0);
-        else
+        else if (!launch_wave_re<Tr::fp64, Tr::ch>(h, H, T, R, rs, tm1, tm2, tout, lv, partial, m, slot_norm, 0, s2))
           k_cheb_re<Tr::fp64, Tr::ch><<<nb, h->threads, smem_bytes(h, R, 3), s2>>>(H, blk, R, rs, tm1, tm2, tout, lv,
                                                                                    partial, nb, m, slot_norm, 0);
         check_launch("k_cheb");
@@ -706,6 +761,15 @@ gqt_status gqt_set_graphs(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_graphs = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_variant(gqt_ham* h, int variant) {
+  API_BEGIN
+  require(h != nullptr && variant >= 0 && variant <= 2, "gqt_set_variant: variant must be 0, 1 or 2");
+  h->variant = variant;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
   API_END
 }
 
@@ -1153,7 +1217,7 @@ extern "C" gqt_status gqt_kpm_weights(int M, const double* d_E, int NE, const do
 // Autotuner: times the fused moment kernel (Re <l|T_m|r> orders, the VAC inner
 // loop) on zero-filled scratch vectors of the handle for each launch shape and
 // keeps the fastest.  Candidates: threads per CTA x CTAs per SM.
-extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_per_sm, void* stream) {
+extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_per_sm, int* variant, void* stream) {
   API_BEGIN
   check_common(h, R);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1164,6 +1228,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   check_cuda(cudaMemsetAsync(l, 0, vb, st), "memset");
   const int cand_t[] = {128, 256, 512};
   const int cand_b[] = {2, 4, 8};
+  const int cand_v[] = {0, 1, 2};
   const int M = 12;
   DevBuf scratch_mu;
   scratch_mu.ensure((size_t)h->nseg * R * M * sizeof(double));
@@ -1173,10 +1238,13 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   const bool graphs = h->use_graphs;
   h->use_graphs = false;
   float best = 1e30f;
-  int bt = h->threads, bb = h->blocks_per_sm;
+  int bt = h->threads, bb = h->blocks_per_sm, bv = h->variant;
   try {
+    for (int v : cand_v)
     for (int t : cand_t)
       for (int b : cand_b) {
+        if (v != 0 && t > 256) continue;
+        h->variant = v;
         h->threads = t;
         h->blocks_per_sm = b;
         h->tables.clear();
@@ -1191,6 +1259,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
           best = ms;
           bt = t;
           bb = b;
+          bv = v;
         }
       }
   } catch (...) {
@@ -1204,6 +1273,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   h->use_graphs = graphs;
   h->threads = bt;
   h->blocks_per_sm = bb;
+  h->variant = bv;
   h->tables.clear();
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
   h->graphs.clear();
@@ -1211,5 +1281,6 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   check_cuda(cudaStreamSynchronize(st), "gqt_autotune");
   if (threads) *threads = bt;
   if (blocks_per_sm) *blocks_per_sm = bb;
+  if (variant) *variant = bv;
   API_END
 }

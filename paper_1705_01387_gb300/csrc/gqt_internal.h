@@ -40,6 +40,7 @@ struct DevBuf {
 struct BlockTable {
   int nblocks = 0;
   DevBuf d_blk, d_seg_blk;
+  DevBuf d_tab4;  // int4 per CTA: segment begin, segment end, rank q in the segment's CTAs, their count G
 };
 
 enum WorkSlot {
@@ -79,6 +80,7 @@ struct gqt_ham {
   int* h_flag = nullptr;  // pinned
   int threads = 256;
   int blocks_per_sm = 0;
+  int variant = 2;  // moment kernels: 0 chunk order, 1 wavefront, 2 wavefront with two elements per thread
   bool use_graphs = true;
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;

@@ -1010,3 +1010,149 @@ __global__ void k_kpm_weights(const double* __restrict__ tab, int M, int NE, con
   }
 }
 }  // namespace gqt
+
+namespace gqt {
+
+// ------------------------------------------- wavefront-ordered moment kernels
+//
+// The CTAs of a segment stride through it together: CTA b with tile entry
+// (beg, end, q, G) handles elements beg*R + (q + j*G)*blockDim + tid.  At any
+// moment the segment's CTAs work on one window of G*blockDim consecutive
+// elements, so neighbour gathers (a few lattice rows away) hit in L2 and
+// T_{m-1} is read from DRAM about once per order.  Each thread keeps U
+// elements in flight: all independent loads of the U elements are issued
+// before the dependent neighbour gathers and the arithmetic.
+
+template <bool FP64, bool CH, int U, bool DBL, int KK>
+__device__ __forceinline__ void cheb_wave_body(const Ell<FP64, CH>& H, int4 tb, int R, int rs,
+                                               const typename Prec<FP64>::V* __restrict__ tm1,
+                                               const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                               const typename Prec<FP64>::V* __restrict__ l, int first,
+                                               DotAcc<typename Prec<FP64>::V>& d0, DotAcc<typename Prec<FP64>::V>& d1,
+                                               DotAcc<typename Prec<FP64>::V>& nl, DotAcc<typename Prec<FP64>::V>& nr) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  using HT = typename Ell<FP64, CH>::HT;
+  constexpr int KMAX = KK;  // neighbour slots, a compile-time constant
+  const size_t segb = (size_t)tb.x << rs, sege = (size_t)tb.y << rs;
+  const size_t step = (size_t)tb.w * blockDim.x;
+  const int r = threadIdx.x & (R - 1);
+  constexpr int K = KK;
+  for (size_t e0 = segb + (size_t)tb.z * blockDim.x + threadIdx.x; e0 < sege; e0 += (size_t)U * step) {
+    V own[U], acc[U], lv[U];
+    int idx[U][KMAX];
+    HT hv[U][KMAX];
+    S dg[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t e = e0 + u * step;
+      ok[u] = e < sege;
+      const size_t ee = ok[u] ? e : e0;
+      const int i = (int)(ee >> rs);
+      own[u] = __ldg(tm1 + ee);
+      dg[u] = __ldg(H.diag2 + i);
+      if (DBL) {
+        if (first) {
+          acc[u].x = 0;
+          acc[u].y = 0;
+        } else {
+          acc[u] = cneg(tm2[ee]);
+        }
+      } else {
+        lv[u] = __ldg(l + ee);
+        if (first) {
+          acc[u].x = 0;
+          acc[u].y = 0;
+        } else {
+          acc[u] = cneg(tm2[ee]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+          const size_t s = (size_t)k * H.n + i;
+          idx[u][k] = __ldg(H.idx + s);
+          hv[u][k] = __ldg(H.hop2 + s);
+        }
+    }
+    V nbv[U][KMAX];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) nbv[u][k] = __ldg(tm1 + (((size_t)idx[u][k] << rs) + r));
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      V a = cmul_acc(acc[u], dg[u], own[u]);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) a = cmul_acc(a, hv[u][k], nbv[u][k]);
+      if (first) a = cscale(a, (S)0.5);
+      if (ok[u]) {
+        tout[e0 + u * step] = a;
+        if (DBL) {
+          d0.add_norm(own[u]);
+          d1.add_re(a, own[u]);
+        } else {
+          if (first) {
+            d0.add_re(lv[u], own[u]);
+            nl.add_norm(lv[u]);
+            nr.add_norm(own[u]);
+          }
+          d1.add_re(lv[u], a);
+        }
+      }
+    }
+  }
+}
+
+// Re <l|T_m|r> orders (VAC rows) in wavefront order; slots as k_cheb_re.
+template <bool FP64, bool CH, int U, int KK>
+__global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_re_w(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int rs,
+                                                   const typename Prec<FP64>::V* __restrict__ tm1,
+                                                   const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                                   const typename Prec<FP64>::V* __restrict__ l,
+                                                   double2* __restrict__ partial, int nblocks, int slot0, int slot_norm,
+                                                   int first) {
+  using V = typename Prec<FP64>::V;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  DotAcc<V> d0, d1, nl, nr;
+  cheb_wave_body<FP64, CH, U, false, KK>(H, tab[b], R, rs, tm1, tm2, tout, l, first, d0, d1, nl, nr);
+  if (first) {
+    double2 v[3] = {d0.get(), d1.get(), make_double2(nl.get().x, nr.get().x)};
+    block_reduce_r<3>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(slot0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+      partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
+    }
+  } else {
+    double2 v[1] = {d1.get()};
+    block_reduce_r<1>(v, R, smem);
+    if ((int)threadIdx.x < R) partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+  }
+}
+
+// l = r doubling orders (DOS, MSD rows) in wavefront order; slots as k_cheb_dbl.
+template <bool FP64, bool CH, int U, int KK>
+__global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_dbl_w(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int rs,
+                                                    const typename Prec<FP64>::V* __restrict__ tm1,
+                                                    const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                                    double2* __restrict__ partial, int nblocks, int m) {
+  using V = typename Prec<FP64>::V;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  DotAcc<V> a0, a1, u0, u1;
+  cheb_wave_body<FP64, CH, U, true, KK>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, m == 1, a0, a1, u0, u1);
+  double2 v[2] = {a0.get(), a1.get()};
+  block_reduce_r<2>(v, R, smem);
+  if ((int)threadIdx.x < R) {
+    const int k0 = 2 * m - 2;
+    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
+    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+  }
+}
+
+}  // namespace gqt

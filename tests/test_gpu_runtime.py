@@ -50,8 +50,8 @@ def test_autotune_and_launch_shapes_keep_results():
     phi = S.random_phase(lat.n, 8, seed=6)
     d = torch.from_numpy(phi).cuda()
     ref = O.Hamiltonian(lat, dE).dos_moments(phi[:, 3], 128)
-    thr, bps = g.gqt_autotune(ham, 8)
-    assert thr in (128, 256, 512) and bps in (2, 4, 8)
+    thr, bps, var = g.gqt_autotune(ham, 8)
+    assert thr in (128, 256, 512) and bps in (2, 4, 8) and var in (0, 1, 2)
     for t, b in ((thr, bps), (128, 2), (512, 8), (256, 4)):
         g.gqt_set_launch(ham, t, b)
         mu = np.empty((1, 8, 128))
@@ -164,3 +164,36 @@ def test_forward_then_backward_evolution_on_one_handle():
         g.gqt_evolve(ham, psi, 2, 0.74, 1)
         g.gqt_evolve(ham, psi, 2, 0.74, -1)
     assert float((psi - phi).abs().max()) < 1e-13
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("name", ["chain", "honeycomb", "square", "cubic_fp32"])
+def test_moment_kernel_variants_agree_with_oracle(variant, name):
+    """Chunk-ordered and wavefront-ordered (one or two elements per thread) moment
+    kernels: DOS (l = r) and VAC-type (Re <l|T|r>) moments equal the oracle's."""
+    if name == "chain":
+        lat, dE, prec = S.chain(3001, -1.0, 4.0, seed=2), 4.2, g.GQT_FP64
+    elif name == "honeycomb":
+        lat, dE, prec = S.honeycomb(45, 31, -2.7, 1.0, seed=3), S.energy_scale_rule(3, -2.7, 1.0), g.GQT_FP64
+    elif name == "square":
+        lat, dE, prec = S.with_random_bond_phases(S.square(33, 29, -1.0, 2.0, seed=4), 5), 5.2, g.GQT_FP64
+    else:
+        lat, dE, prec = S.cubic(15, -1.0, 16.5, seed=6), S.energy_scale_rule(6, -1.0, 16.5), g.GQT_FP32_ACC64
+    ham = g.gqt_build_hamiltonian(lat, dE, prec)
+    g.gqt_set_variant(ham, variant)
+    R = 4
+    ph = S.random_phase(lat.n, R, seed=8)
+    cd = torch.complex128 if prec == g.GQT_FP64 else torch.complex64
+    d = torch.from_numpy(ph).to(cd).cuda()
+    M = 97
+    mu = np.empty((1, R, M))
+    g.gqt_dos_moments(ham, d, R, M, mu)
+    h = O.Hamiltonian(lat, dE)
+    tol = 1e-10 if prec == g.GQT_FP64 else 2e-5
+    for r in (0, 3):
+        assert nerr(mu[0, r], h.dos_moments(ph[:, r], M)) < tol
+    # VAC row 0: Re <V phi | T_n | V phi>
+    vac = _vac(ham, d, np.array([0.5]), M, [O.np_rule(dE * 0.5, 64)])
+    for r in (0, 3):
+        ref = h.vac_moments(ph[:, r], np.array([0.5]), [O.np_rule(dE * 0.5, 64)], M)[0]
+        assert nerr(vac[0, 0, r], ref) < (1e-10 if prec == g.GQT_FP64 else 1e-4)
