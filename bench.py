@@ -123,6 +123,53 @@ def bytes_per_orbital_cheb(K: int, fp64: bool, hop_real: bool, R: int) -> float:
     return 4 * v * R + K * (4 + hop) + s
 
 
+def fp64_fma_per_orbital(K: int, hop_real: bool, dot: str) -> int:
+    """Algorithmic FP64 fused multiply-adds per orbital per order: the recurrence
+    (diagonal 2, each neighbour 2 real or 4 complex) plus the moment dot products
+    (Re <l|T_m>: 2; the l = r kernel's <u|u> and Re <u_m|u_m-1>: 4)."""
+    return 2 + K * (2 if hop_real else 4) + (2 if dot == "re" else 4)
+
+
+def fp32_batched(args, g, torch):
+    """Batched FP32 form vs plain FP64 on the simple-cubic Anderson model L = 256
+    (N = 16,777,216, 6 neighbours, t = -1, W = 16.5): DOS moments for R = 32 FP32
+    vectors in one launch sequence vs one FP64 vector, per orbital-moment."""
+    w = S.config(2, small=args.small)
+    L = args.fp32_L or w.lattice_args["L"]
+    M = args.fp32_moments
+    out = {"workload": f"cubic{L}_W16.5", "moments": M}
+    res = {}
+    for prec, R in ((g.GQT_FP32_ACC64, w.R), (g.GQT_FP64, 1)):
+        ham = g.gqt_build_hamiltonian(None, w.energy_scale, prec, kind=g.GQT_LATTICE_CUBIC, L1=L, t=-1.0,
+                                      W=16.5, seed=w.seed)
+        cd = torch.complex64 if prec == g.GQT_FP32_ACC64 else torch.complex128
+        phi = torch.empty((ham.n, R), dtype=cd, device="cuda")
+        g.gqt_random_phase(ham, w.seed, R, phi)
+        mu = torch.empty((1, R, M), dtype=torch.float64, device="cuda")
+        g.gqt_dos_moments(ham, phi, R, M, mu)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            g.gqt_dos_moments(ham, phi, R, M, mu)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 2 * 1e-3
+        res[prec] = (ham.n * R * M / t, mu[0, 0].cpu().numpy(), t, R, ham.n)
+        del phi, ham
+        torch.cuda.empty_cache()
+    v32, mu32, t32, R32, n = res[g.GQT_FP32_ACC64]
+    v64, mu64, t64, _, _ = res[g.GQT_FP64]
+    # FP32 storage reads 8 B per vector element (T_m-1, T_m-2, T_m) and H~ once for all R vectors
+    bpo32 = (3 * 8 * R32 + 6 * (4 + 4) + 4) / R32
+    hbm, _ = _peaks()
+    out.update({"fp32_R": R32, "fp32_orbital_moments_per_s": v32, "fp64_orbital_moments_per_s": v64,
+                "speedup": v32 / v64, "fp32_ms": t32 * 1e3, "fp64_ms": t64 * 1e3,
+                "fp32_hbm_frac": v32 / 2 * bpo32 / 1e9 / hbm,
+                "dos_moment_error_fp32_vs_fp64": float(np.max(np.abs(mu32 - mu64)) / np.max(np.abs(mu64)))})
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1705_01387_gb300 as g
@@ -223,6 +270,11 @@ def run_ours(args):
     n_launch = int(prof_n[dom])
     avg_s = prof_ms[dom] * 1e-3 / max(n_launch, 1)
     achieved = N * bpo / avg_s / 1e9
+    # FP64 arithmetic roofline of the same kernel against the measured FMA peak
+    fp64_peak = g.gqt_probe_fp64()
+    fma = fp64_fma_per_orbital(3, ham.hop_real, "re" if dom == 1 else "dbl") * R
+    fp64_achieved = 2.0 * fma * N / avg_s / 1e9
+    hbm_frac, alu_frac = achieved / hbm, fp64_achieved / fp64_peak
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -234,14 +286,24 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (H~ ELL %.2f GB + state vectors)" % (N * (3 * 12 + 8 + 24) / 1e9),
                    "parallelism": f"replicas x{ws} (independent random vectors)"},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": kname, "bytes_per_orbital": bpo, "avg_launch_us": avg_s * 1e6,
-                     "launches": n_launch,
-                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                     "kernel_share_of_timed": prof_ms[dom] / max(total_prof, 1e-12), "families": fams},
+        "roofline": ({"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                      "frac": alu_frac, "traffic": None, "kernel": kname, "fp64_fma_per_orbital": fma,
+                      "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)",
+                      "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+                              "bytes_per_orbital": bpo}}
+                     if alu_frac > hbm_frac else
+                     {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+                      "traffic": None, "kernel": kname, "bytes_per_orbital": bpo,
+                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                      "fp64": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s", "frac": alu_frac,
+                               "fp64_fma_per_orbital": fma}}),
+        "kernels": {"dominant": kname, "avg_launch_us": avg_s * 1e6, "launches": n_launch,
+                    "share_of_timed_kernels": prof_ms[dom] / max(total_prof, 1e-12), "families": fams},
         "e2e": e2e,
         "clocks": clk.summary(),
     }
+    if rank == 0 and not args.no_fp32:
+        out["fp32_batched"] = fp32_batched(args, g, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.small, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -313,9 +375,17 @@ def main():
     ap.add_argument("--cells", default=None, help="L1xL2 honeycomb cells (profiling captures only)")
     ap.add_argument("--moments", type=int, default=None, help="moments per row (profiling captures only)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the batched FP32 vs FP64 comparison")
+    ap.add_argument("--fp32-moments", type=int, default=512, help="moments of the FP32/FP64 comparison")
+    ap.add_argument("--fp32-L", type=int, default=0, help="cubic L of the FP32 comparison (profiling captures only)")
+    ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_fp32:
+        import torch
+        import paper_1705_01387_gb300 as g
+        print(json.dumps(fp32_batched(args, g, torch)))
     else:
         run_ours(args)
 

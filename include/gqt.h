@@ -221,8 +221,9 @@ int gqt_np_rule(double x, int cap);
 gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
 /* Moment-kernel variant: 0 = each CTA walks one contiguous chunk of sites; 1 =
  * wavefront order (the CTAs of a segment stride through it together, so
- * neighbour gathers hit in L2); 2 = wavefront with two elements in flight per
- * thread.  Variants 1-2 cover 2, 3, 4 or 6 neighbour slots and up to 256
+ * neighbour gathers hit in L2); 2 = wavefront with more work in flight per
+ * thread: two sites per thread for R = 1, and for R >= 2 one site's 2 (R = 2)
+ * or 4 (R >= 4) consecutive vectors per thread, sharing one load of its H~ row.  Variants 1-2 cover 2, 3, 4 or 6 neighbour slots and up to 256
  * threads per CTA; otherwise variant 0 runs.  Default 2.  gqt_autotune also
  * chooses the variant. */
 gqt_status gqt_set_variant(gqt_ham* ham, int variant);
@@ -265,6 +266,12 @@ gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);
  *  - The call waits for its stream before returning (status check). */
 #define GQT_NOALLOC_SCRATCH_BYTES (4u << 20)
 gqt_status gqt_dos_moments_noalloc(const gqt_ham* ham, const void* d_phi, int R, int M, double* d_mu, void* stream);
+
+/* Measured FP64 fused-multiply-add throughput of the current GPU in GFLOP/s
+ * (an FMA counts 2 flops): best of five timed launches of a kernel running 8
+ * independent FMA chains per thread on every SM.  The peak of the FP64
+ * arithmetic roofline. */
+gqt_status gqt_probe_fp64(double* gflops, void* stream);
 
 /* Number of kernel launches the library has enqueued since load (for accounting). */
 uint64_t gqt_launch_count(void);

@@ -66,6 +66,7 @@ _SIGS = {
     "gqt_set_variant": [_P, _I],
     "gqt_launch_count": [],
     "gqt_profile_start": [],
+    "gqt_probe_fp64": [_P, _P],
     "gqt_profile_stop": [_P, _P, _I],
     "gqt_last_error": [],
     "gqt_dos_moments_noalloc": [_P, _P, _I, _I, _P, _P],
@@ -364,6 +365,13 @@ def gqt_profile_stop(ncat: int = 5):
     n = np.zeros(ncat, np.uint64)
     _check(lib().gqt_profile_stop(ms.ctypes.data, n.ctypes.data, int(ncat)))
     return ms, n
+
+
+def gqt_probe_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput (GFLOP/s) of the current GPU."""
+    v = C.c_double()
+    _check(lib().gqt_probe_fp64(C.byref(v), _stream(stream)))
+    return v.value
 
 
 def gqt_launch_count() -> int:

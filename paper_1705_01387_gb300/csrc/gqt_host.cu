@@ -370,7 +370,13 @@ static bool launch_wave_re(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable&
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_RE(KK)                                                                                          \
-  if (h->variant == 1)                                                                                           \
+  if (h->variant == 2 && R >= 4)                                                                                 \
+    k_cheb_re_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, l,       \
+                                                                     partial, T.nblocks, slot0, slot_norm, first); \
+  else if (h->variant == 2 && R == 2)                                                                            \
+    k_cheb_re_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, l,       \
+                                                                     partial, T.nblocks, slot0, slot_norm, first); \
+  else if (h->variant == 1)                                                                                      \
     k_cheb_re_w<FP64, CH, 1, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, l, partial, \
                                                                     T.nblocks, slot0, slot_norm, first);       \
   else                                                                                                           \
@@ -394,7 +400,13 @@ static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_DBL(KK)                                                                                           \
-  if (h->variant == 1)                                                                                             \
+  if (h->variant == 2 && R >= 4)                                                                                   \
+    k_cheb_dbl_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, partial, \
+                                                                      T.nblocks, m);                              \
+  else if (h->variant == 2 && R == 2)                                                                              \
+    k_cheb_dbl_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, partial, \
+                                                                      T.nblocks, m);                              \
+  else if (h->variant == 1)                                                                                        \
     k_cheb_dbl_w<FP64, CH, 1, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, tm1, tm2, tout, partial,     \
                                                                      T.nblocks, m);                               \
   else                                                                                                             \
@@ -1282,5 +1294,35 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   if (threads) *threads = bt;
   if (blocks_per_sm) *blocks_per_sm = bb;
   if (variant) *variant = bv;
+  API_END
+}
+
+// Measured FP64 FMA throughput of the current GPU (GFLOP/s, an FMA = 2 flops):
+// best of five launches of a kernel with 8 independent FMA chains per thread on
+// every SM.  Used as the peak of the FP64 arithmetic roofline.
+extern "C" gqt_status gqt_probe_fp64(double* gflops, void* stream) {
+  API_BEGIN
+  require(gflops != nullptr, "gqt_probe_fp64: null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = sm_count() * 8, threads = 256, iters = 4096;
+  DevBuf sink;
+  sink.ensure((size_t)blocks * sizeof(double));
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  float best = 1e30f;
+  for (int rep = 0; rep < 6; ++rep) {
+    check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
+    k_probe_dfma<<<blocks, threads, 0, st>>>((double*)sink.p, iters, 0.9999999, 1e-7);
+    check_launch("k_probe_dfma");
+    check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
+    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *gflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e9;
   API_END
 }

@@ -117,9 +117,9 @@ __device__ __forceinline__ double2 cfma_d(double2 acc, double2 c, V t) {
 // Dot-product accumulators: conj(l) * t summed over a thread's elements.
 // FP64: plain FMA chains.  FP32: the products and sums run in FP32 with the
 // error-free transformations of Ogita, Rump and Oishi ("Accurate sum and dot
-// product", SIAM J. Sci. Comput. 26, 2005: TwoProduct by fmaf, TwoSum), and
-// the compensated (hi, lo) pair is folded into an FP64 total every 16 terms,
-// so FP64 work per element stays far below one operation.
+// product", SIAM J. Sci. Comput. 26, 2005: TwoProduct by fmaf, TwoSum); the
+// compensated (hi, lo) pair becomes FP64 once per thread and the CTA and
+// segment sums run in FP64.
 template <class V>
 struct DotAcc;
 
@@ -159,40 +159,34 @@ struct CompF {
     hi = s;
     lo += e + pe;
   }
+  __device__ __forceinline__ void add_val(float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo += e;
+  }
 };
 
+// The (hi, lo) pair is converted to FP64 once per thread, in get(): the
+// compensated sum of n products is accurate to about n * 2^-48 of the sum of
+// their magnitudes (Dot2 bound), far below the FP32 rounding of the vectors,
+// and FP32->FP64 conversions run on the narrow FP64 pipe, so converting per
+// element would make the kernel FP64-bound.
 template <>
 struct DotAcc<float2> {
   CompF re, im;
-  double2 s = make_double2(0.0, 0.0);
-  int cnt = 0;
-  __device__ __forceinline__ void flush() {
-    s.x += (double)re.hi + (double)re.lo;
-    s.y += (double)im.hi + (double)im.lo;
-    re = CompF();
-    im = CompF();
-    cnt = 0;
-  }
   __device__ __forceinline__ void add(float2 l, float2 t) {
     re.add_prod(l.x, t.x);
     re.add_prod(l.y, t.y);
     im.add_prod(l.x, t.y);
     im.add_prod(-l.y, t.x);
-    if (++cnt == 16) flush();
   }
-  __device__ __forceinline__ void add_norm(float2 t) {
-    re.add_prod(t.x, t.x);
-    re.add_prod(t.y, t.y);
-    if (++cnt == 16) flush();
-  }
-  __device__ __forceinline__ void add_re(float2 l, float2 t) {
-    re.add_prod(l.x, t.x);
-    re.add_prod(l.y, t.y);
-    if (++cnt == 16) flush();
-  }
+  // Real-valued terms (norms, Re conj(l) t): the element's value is formed with one
+  // rounding (fmaf) and then added with TwoSum, so only the sum is compensated.
+  __device__ __forceinline__ void add_norm(float2 t) { re.add_val(fmaf(t.x, t.x, t.y * t.y)); }
+  __device__ __forceinline__ void add_re(float2 l, float2 t) { re.add_val(fmaf(l.x, t.x, l.y * t.y)); }
   __device__ __forceinline__ double2 get() {
-    flush();
-    return s;
+    return make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
   }
 };
 
@@ -321,7 +315,7 @@ __global__ void k_cheb(Ell<FP64, CH> H, const int* __restrict__ blk, int R, int 
 // CTA order, of partial[m][b][r].  mode 0: complex out (double2), mode 1: real
 // part (double).  Bound check: |mu_m|^2 <= bound_factor |l|^2 |r|^2 (norms
 // from slot slot_norm), failure sets bit 1 of *flag; NaN/Inf sets bit 2.
-__global__ void k_reduce(const double2* __restrict__ partial, int nslots_m, int nblocks, int R,
+static __global__ void k_reduce(const double2* __restrict__ partial, int nslots_m, int nblocks, int R,
                          const int* __restrict__ seg_blk, int nseg, int slot_norm, double bound_factor, void* out,
                          int mode, int* __restrict__ flag) {
   const size_t total = (size_t)nseg * R * nslots_m;
@@ -614,7 +608,7 @@ __global__ void k_cheb_dbl(Ell<FP64, CH> H, const int* __restrict__ blk, int R, 
 
 // Second pass of k_cheb_dbl: mu[s][r][k] = s_k for k < 2, 2 s_k - s_{k mod 2} otherwise,
 // each s summed over the segment's CTAs in CTA order.  Bound |mu_k| <= (1+tol) mu_0.
-__global__ void k_reduce_dbl(const double2* __restrict__ partial, int M, int nblocks, int R,
+static __global__ void k_reduce_dbl(const double2* __restrict__ partial, int M, int nblocks, int R,
                              const int* __restrict__ seg_blk, int nseg, double bound_factor, double* __restrict__ out,
                              int* __restrict__ flag) {
   const size_t total = (size_t)nseg * R * M;
@@ -639,7 +633,7 @@ __global__ void k_reduce_dbl(const double2* __restrict__ partial, int M, int nbl
 // Norm check of an evolution: slots q (before) and NSET + q (after) hold the
 // partial squared norms of set q.  | |after| - |before| | > tol |before| sets
 // bit 3 of *flag.  norms (optional) receives [nseg][R][NSET][2] squared norms.
-__global__ void k_norm_check(const double2* __restrict__ partial, int nset, int nblocks, int R,
+static __global__ void k_norm_check(const double2* __restrict__ partial, int nset, int nblocks, int R,
                              const int* __restrict__ seg_blk, int nseg, double tol, double* __restrict__ norms,
                              int* __restrict__ flag) {
   const int total = nseg * R * nset;
@@ -660,7 +654,7 @@ __global__ void k_norm_check(const double2* __restrict__ partial, int nset, int 
 }
 
 // MSD step: slot 0 = |p|^2 before, slot 2 = |U p|^2 after (slot 3 = |px|^2, unchecked).
-__global__ void k_norm_check_msd(const double2* __restrict__ partial, int nblocks, int R,
+static __global__ void k_norm_check_msd(const double2* __restrict__ partial, int nblocks, int R,
                                  const int* __restrict__ seg_blk, int nseg, double tol, int* __restrict__ flag) {
   const int total = nseg * R;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -711,7 +705,7 @@ __global__ void k_velocity(Ell<FP64, CH> H, const int* __restrict__ blk, int R, 
 
 // tab[n][e] = g_n (2 - delta_n0) cos(n arccos x_e) * 2 n_over_omega / (pi dE sqrt(1 - x_e^2))
 // (Eqs. 25-27, 31); NaN where |x_e| >= 1.
-__global__ void k_kpm_table(int M, const double* __restrict__ E, int NE, double dE, double n_over_omega, int jackson,
+static __global__ void k_kpm_table(int M, const double* __restrict__ E, int NE, double dE, double n_over_omega, int jackson,
                             double* __restrict__ tab) {
   const size_t total = (size_t)M * NE;
   const double a = 1.0 / (M + 1.0);
@@ -732,7 +726,7 @@ __global__ void k_kpm_table(int M, const double* __restrict__ E, int NE, double 
 }
 
 // out[row][e] = sum_n mu[row][n] tab[n][e]: a small FP64 GEMM, 16x16 tiles.
-__global__ void k_kpm_gemm(const double* __restrict__ mu, int rows, int M, const double* __restrict__ tab, int NE,
+static __global__ void k_kpm_gemm(const double* __restrict__ mu, int rows, int M, const double* __restrict__ tab, int NE,
                            double* __restrict__ out) {
   __shared__ double As[16][17], Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -751,7 +745,7 @@ __global__ void k_kpm_gemm(const double* __restrict__ mu, int rows, int M, const
 
 // --------------------------------------------------------------- sigma
 
-__global__ void k_sigma_vac(const double* __restrict__ v, const double* __restrict__ dt, int Nt, int NE,
+static __global__ void k_sigma_vac(const double* __restrict__ v, const double* __restrict__ dt, int Nt, int NE,
                             double* __restrict__ out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NE; e += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -763,7 +757,7 @@ __global__ void k_sigma_vac(const double* __restrict__ v, const double* __restri
   }
 }
 
-__global__ void k_sigma_msd(const double* __restrict__ m, const double* __restrict__ dt, int Nt, int NE,
+static __global__ void k_sigma_msd(const double* __restrict__ m, const double* __restrict__ dt, int Nt, int NE,
                             double* __restrict__ out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NE; e += gridDim.x * blockDim.x) {
     double prev = 0.0;
@@ -983,7 +977,7 @@ __global__ void k_axpy(const int* __restrict__ blk, V* __restrict__ y, const V* 
 }
 
 // Slot-major [K][n] double2 -> row-major [n][K] double2; diagonal copied.
-__global__ void k_grad_out(int n, int K, const double2* __restrict__ gslot, const double* __restrict__ gdiag,
+static __global__ void k_grad_out(int n, int K, const double2* __restrict__ gslot, const double* __restrict__ gdiag,
                            double2* __restrict__ out_slot, double* __restrict__ out_diag) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * K; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / K), k = (int)(t % K);
@@ -998,7 +992,7 @@ namespace gqt {
 // beta[n] = sum_e w[e] tab[n][e]: the transpose of the reconstruction (the weight
 // each moment carries in a weighted sum of reconstructed values).  NaN entries of
 // the table (|E| >= dE) must carry zero weight and are skipped when w[e] == 0.
-__global__ void k_kpm_weights(const double* __restrict__ tab, int M, int NE, const double* __restrict__ w,
+static __global__ void k_kpm_weights(const double* __restrict__ tab, int M, int NE, const double* __restrict__ w,
                               double* __restrict__ beta) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < M; n += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -1153,6 +1147,207 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_dbl_w(Ell<FP64, 
     partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
     partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
   }
+}
+
+}  // namespace gqt
+
+namespace gqt {
+// FP64 FMA throughput probe: 8 independent FMA chains per thread.
+static __global__ void k_probe_dfma(double* __restrict__ sink, int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1e-3 * threadIdx.x + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.0) sink[blockIdx.x] = s;  // never true; keeps the chains alive
+}
+}  // namespace gqt
+
+
+namespace gqt {
+
+// ------------------------------------- several vectors per thread (SpMM form)
+//
+// For R >= 2 each thread handles VPT consecutive vectors of one site: the
+// site's H~ row (indices, hoppings, diagonal) is loaded once for VPT vectors
+// and every vector access is a VPT-wide contiguous load (16-byte loads for
+// FP32 pairs), so instruction count per vector element drops by ~VPT.
+template <int VPT>
+__device__ __forceinline__ void ldg_v(float2 (&d)[VPT], const float2* __restrict__ p) {
+#pragma unroll
+  for (int q = 0; q < VPT; q += 2) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p + q));
+    d[q] = make_float2(t.x, t.y);
+    d[q + 1] = make_float2(t.z, t.w);
+  }
+}
+template <int VPT>
+__device__ __forceinline__ void ld_v(float2 (&d)[VPT], const float2* p) {
+#pragma unroll
+  for (int q = 0; q < VPT; q += 2) {
+    const float4 t = *reinterpret_cast<const float4*>(p + q);
+    d[q] = make_float2(t.x, t.y);
+    d[q + 1] = make_float2(t.z, t.w);
+  }
+}
+template <int VPT>
+__device__ __forceinline__ void st_v(float2* p, const float2 (&d)[VPT]) {
+#pragma unroll
+  for (int q = 0; q < VPT; q += 2) *reinterpret_cast<float4*>(p + q) = make_float4(d[q].x, d[q].y, d[q + 1].x, d[q + 1].y);
+}
+template <int VPT>
+__device__ __forceinline__ void ldg_v(double2 (&d)[VPT], const double2* __restrict__ p) {
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) d[q] = __ldg(p + q);
+}
+template <int VPT>
+__device__ __forceinline__ void ld_v(double2 (&d)[VPT], const double2* p) {
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) d[q] = p[q];
+}
+template <int VPT>
+__device__ __forceinline__ void st_v(double2* p, const double2 (&d)[VPT]) {
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) p[q] = d[q];
+}
+
+// One recurrence order for VPT vectors of each site, wavefront order over groups
+// of VPT vectors (gs = log2(R / VPT)).  DBL: l = r doubling dots; otherwise Re <l|.>.
+template <bool FP64, bool CH, int VPT, bool DBL, int KK>
+__device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, int R, int gs,
+                                              const typename Prec<FP64>::V* __restrict__ tm1,
+                                              const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                              const typename Prec<FP64>::V* __restrict__ l, int first,
+                                              DotAcc<typename Prec<FP64>::V> (&d0)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&d1)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&nl)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&nr)[VPT]) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  const size_t gb = (size_t)tb.x << gs, ge = (size_t)tb.y << gs;
+  const size_t step = (size_t)tb.w * blockDim.x;
+  const int gmask = (1 << gs) - 1;
+  for (size_t gi = gb + (size_t)tb.z * blockDim.x + threadIdx.x; gi < ge; gi += step) {
+    const int i = (int)(gi >> gs);
+    const int r0 = (int)(gi & gmask) * VPT;
+    const size_t base = (size_t)i * R + r0;
+    V own[VPT], acc[VPT], lv[VPT];
+    int idx[KK];
+    typename Ell<FP64, CH>::HT hv[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      idx[k] = __ldg(H.idx + s);
+      hv[k] = __ldg(H.hop2 + s);
+    }
+    const S dg = __ldg(H.diag2 + i);
+    ldg_v<VPT>(own, tm1 + base);
+    if (first) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        acc[v].x = 0;
+        acc[v].y = 0;
+      }
+    } else {
+      ld_v<VPT>(acc, tm2 + base);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) acc[v] = cneg(acc[v]);
+    }
+    if (!DBL) ldg_v<VPT>(lv, l + base);
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      V nb[VPT];
+      ldg_v<VPT>(nb, tm1 + (size_t)idx[k] * R + r0);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) acc[v] = cmul_acc(acc[v], hv[k], nb[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      acc[v] = cmul_acc(acc[v], dg, own[v]);
+      if (first) acc[v] = cscale(acc[v], (S)0.5);
+    }
+    st_v<VPT>(tout + base, acc);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      if (DBL) {
+        d0[v].add_norm(own[v]);
+        d1[v].add_re(acc[v], own[v]);
+      } else {
+        if (first) {
+          d0[v].add_re(lv[v], own[v]);
+          nl[v].add_norm(lv[v]);
+          nr[v].add_norm(own[v]);
+        }
+        d1[v].add_re(lv[v], acc[v]);
+      }
+    }
+  }
+}
+
+template <int VPT, int NQ>
+__device__ __forceinline__ void write_partials_vpt(double2 (&v)[NQ * VPT], int R, int G, double2* smem,
+                                                   double2* __restrict__ partial, int nblocks, const int (&slot)[NQ]) {
+  block_reduce_r<NQ * VPT>(v, G, smem);
+  if ((int)threadIdx.x < G) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int w = 0; w < VPT; ++w)
+        partial[((size_t)slot[q] * nblocks + blockIdx.x) * R + threadIdx.x * VPT + w] = v[q * VPT + w];
+  }
+}
+
+template <bool FP64, bool CH, int VPT, int KK>
+__global__ void __launch_bounds__(256, 2) k_cheb_re_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+                                                       const typename Prec<FP64>::V* __restrict__ tm1,
+                                                       const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                                       const typename Prec<FP64>::V* __restrict__ l,
+                                                       double2* __restrict__ partial, int nblocks, int slot0,
+                                                       int slot_norm, int first) {
+  using V = typename Prec<FP64>::V;
+  DotAcc<V> d0[VPT], d1[VPT], nl[VPT], nr[VPT];
+  cheb_wave_vpt<FP64, CH, VPT, false, KK>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, first, d0, d1, nl, nr);
+  const int G = 1 << gs;
+  if (first) {
+    double2 v[3 * VPT];
+#pragma unroll
+    for (int w = 0; w < VPT; ++w) {
+      v[w] = d0[w].get();
+      v[VPT + w] = d1[w].get();
+      v[2 * VPT + w] = make_double2(nl[w].get().x, nr[w].get().x);
+    }
+    const int slots[3] = {slot0, slot0 + 1, slot_norm};
+    write_partials_vpt<VPT, 3>(v, R, G, dyn_smem(), partial, nblocks, slots);
+  } else {
+    double2 v[VPT];
+#pragma unroll
+    for (int w = 0; w < VPT; ++w) v[w] = d1[w].get();
+    const int slots[1] = {slot0};
+    write_partials_vpt<VPT, 1>(v, R, G, dyn_smem(), partial, nblocks, slots);
+  }
+}
+
+template <bool FP64, bool CH, int VPT, int KK>
+__global__ void __launch_bounds__(256, 2) k_cheb_dbl_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+                                                        const typename Prec<FP64>::V* __restrict__ tm1,
+                                                        const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
+                                                        double2* __restrict__ partial, int nblocks, int m) {
+  using V = typename Prec<FP64>::V;
+  DotAcc<V> a0[VPT], a1[VPT], u0[VPT], u1[VPT];
+  cheb_wave_vpt<FP64, CH, VPT, true, KK>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, m == 1, a0, a1, u0, u1);
+  double2 v[2 * VPT];
+#pragma unroll
+  for (int w = 0; w < VPT; ++w) {
+    v[w] = a0[w].get();
+    v[VPT + w] = a1[w].get();
+  }
+  const int slots[2] = {2 * m - 2, 2 * m - 1};
+  write_partials_vpt<VPT, 2>(v, R, 1 << gs, dyn_smem(), partial, nblocks, slots);
 }
 
 }  // namespace gqt
