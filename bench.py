@@ -170,6 +170,68 @@ def fp32_batched(args, g, torch):
     return out
 
 
+def precision_table(args, g, torch):
+    """Per-result error of the FP32-storage form against the FP64 path on the
+    honeycomb 2048 x 2048 lattice with 1% vacancies (N = 8,388,608, W = 0.5 eV,
+    R = 8, M = 4000, dt = 2 hbar/|t|): DOS moments and reconstructed DOS, VAC
+    moments, rho*C_vv(E) and sigma_VAC(E, t) over the first steps, MSD moments,
+    rho*dX^2(E) and sigma_MSD.  Errors are normalised L-infinity over E (and n)."""
+    w = S.config(3, small=args.small)
+    L1 = w.lattice_args["L1"]
+    M, R, Nt = w.M, w.R, args.precision_steps
+    dE = w.energy_scale
+    res = {}
+    E = torch.from_numpy(w.energies).cuda()
+    dts = np.full(Nt, w.dt)
+    for prec in (g.GQT_FP64, g.GQT_FP32_ACC64):
+        ham = g.gqt_build_hamiltonian(None, dE, prec, kind=g.GQT_LATTICE_HONEYCOMB, L1=L1, L2=L1, t=-2.7, W=0.5,
+                                      vacancy_frac=0.01, seed=w.seed)
+        nO = ham.n / ham.volume
+        cd = torch.complex128 if prec == g.GQT_FP64 else torch.complex64
+        phi = torch.empty((ham.n, R), dtype=cd, device="cuda")
+        g.gqt_random_phase(ham, w.seed, R, phi)
+        dos = torch.empty((1, R, M), dtype=torch.float64, device="cuda")
+        g.gqt_dos_moments(ham, phi, R, M, dos)
+        a, b = torch.empty_like(phi), torch.empty_like(phi)
+        g.gqt_vac_init(ham, phi, a, b, R)
+        vac = torch.empty((Nt, 1, R, M), dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        g.gqt_vac_moments(ham, a, b, R, dts, M, vac)
+        torch.cuda.synchronize()
+        t_vac = time.perf_counter() - t0
+        p, px = torch.empty_like(phi), torch.empty_like(phi)
+        g.gqt_msd_init(ham, phi, p, px, R)
+        msd = torch.empty((Nt, 1, R, M), dtype=torch.float64, device="cuda")
+        g.gqt_msd_moments(ham, p, px, R, dts, M, msd)
+        out = {"dos_mu": dos[0].cpu().numpy(), "vac_mu": vac[:, 0].cpu().numpy(), "msd_mu": msd[:, 0].cpu().numpy(),
+               "t_vac": t_vac}
+        # reconstruction, vector 0 (rows over time)
+        for key, rows in (("dos", dos[0, :1]), ("vac", vac[:, 0, 0].contiguous()), ("msd", msd[:, 0, 0].contiguous())):
+            rec = torch.empty((rows.shape[0], E.numel()), dtype=torch.float64, device="cuda")
+            g.gqt_kpm_reconstruct(rows.contiguous(), E, dE, nO, rec)
+            out[key] = rec
+        sv = torch.empty_like(out["vac"])
+        g.gqt_sigma_vac(out["vac"], dts, sv)
+        sm = torch.empty_like(out["msd"])
+        g.gqt_sigma_msd(out["msd"], dts, sm)
+        out["sigma_vac"], out["sigma_msd"] = sv, sm
+        for k in ("dos", "vac", "msd", "sigma_vac", "sigma_msd"):
+            out[k] = out[k].cpu().numpy()
+        res[prec] = out
+        del ham, phi, a, b, p, px
+        torch.cuda.empty_cache()
+
+    def nerr(x, y):
+        return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
+
+    r64, r32 = res[g.GQT_FP64], res[g.GQT_FP32_ACC64]
+    tab = {k: nerr(r32[k], r64[k]) for k in ("dos_mu", "vac_mu", "msd_mu", "dos", "vac", "msd", "sigma_vac",
+                                             "sigma_msd")}
+    return {"workload": f"honeycomb{L1}x{L1}_vac1pct_R{R}_M{M}", "steps": Nt, "errors_fp32_vs_fp64": tab,
+            "vac_seconds_fp64": r64["t_vac"], "vac_seconds_fp32": r32["t_vac"],
+            "vac_speedup_fp32": r64["t_vac"] / r32["t_vac"]}
+
+
 def run_ours(args):
     import torch
     import paper_1705_01387_gb300 as g
@@ -379,9 +441,15 @@ def main():
     ap.add_argument("--fp32-moments", type=int, default=512, help="moments of the FP32/FP64 comparison")
     ap.add_argument("--fp32-L", type=int, default=0, help="cubic L of the FP32 comparison (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
+    ap.add_argument("--precision", action="store_true", help="FP32 vs FP64 per-result error table (C4 workload)")
+    ap.add_argument("--precision-steps", type=int, default=3, help="VAC/MSD time steps of the error table")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.precision:
+        import torch
+        import paper_1705_01387_gb300 as g
+        print(json.dumps(precision_table(args, g, torch)))
     elif args.only_fp32:
         import torch
         import paper_1705_01387_gb300 as g
