@@ -235,6 +235,7 @@ def precision_table(args, g, torch):
 def run_ours(args):
     import torch
     import paper_1705_01387_gb300 as g
+    from paper_1705_01387_gb300.replicas import max_over_ranks, shard_vectors
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -249,7 +250,8 @@ def run_ours(args):
     del lat
     cd = torch.complex128
     phi = torch.empty((N, R), dtype=cd, device="cuda")
-    g.gqt_random_phase(ham, w.seed, R, phi, first_vector=rank)
+    first, _ = shard_vectors(ws * R, ws, rank)  # one independent random vector per rank
+    g.gqt_random_phase(ham, w.seed, R, phi, first_vector=first)
     a, b, p, px = (torch.empty_like(phi) for _ in range(4))
     g.gqt_vac_init(ham, phi, a, b, R)
     g.gqt_msd_init(ham, phi, p, px, R)
@@ -284,9 +286,7 @@ def run_ours(args):
     launches = g.gqt_launch_count() - launches0
     t_ms = e0.elapsed_time(e1)
     if ws > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+        t_ms = max_over_ranks(t_ms, device="cuda")
     units = float(N) * 2 * M * args.steps * ws
     value = units / (t_ms * 1e-3)
 

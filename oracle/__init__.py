@@ -36,11 +36,24 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_override_path = None
+
+
+def use_library(path):
+    """Load the oracle from another shared object (a test builds deliberately
+    broken copies to show that the pins catch each mistake); None restores the
+    regular build."""
+    global _lib, _override_path
+    with _lock:
+        _lib = None
+        _override_path = path
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(_override_path or build())
             L.orc_ham_new.restype = C.c_void_p
             L.orc_ham_new.argtypes = [C.c_int64, C.c_int, _i32, _i32, _d, _d, _d, _d, C.c_double]
             L.orc_ham_free.argtypes = [C.c_void_p]

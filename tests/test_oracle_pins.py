@@ -353,6 +353,9 @@ def test_sigma_rules():
     s = O.sigma_vac(v, dt)
     tv = np.concatenate([[0], np.cumsum(dt)])[:4]
     assert np.allclose(s, 2.5 * tv[:, None], atol=1e-15)
+    # rho C_vv linear in t: the trapezoid rule is exact, integral = a t + b t^2 / 2
+    lin = (1.5 - 0.7 * tv)[:, None] * np.ones((1, 3))
+    assert np.allclose(O.sigma_vac(lin, dt), (1.5 * tv - 0.35 * tv ** 2)[:, None], atol=1e-14)
     tm = np.cumsum(dt)
     m = 3.0 * tm[:, None] ** 2 * np.ones((1, 3))
     sm = O.sigma_msd(m, dt)
