@@ -232,6 +232,60 @@ def precision_table(args, g, torch):
             "vac_speedup_fp32": r64["t_vac"] / r32["t_vac"]}
 
 
+def latency(args, g, torch):
+    """Latency-bound workloads.  C1: honeycomb 32 x 32 (N = 2048) VAC + MSD, 10 steps
+    of 1 hbar/|t|, M = 512, with CUDA graphs on and off (microseconds per moment).
+    C5: honeycomb 256 x 256 (N = 131072), sigma_VAC(E, t_50) loss and its gradient
+    with respect to N on-site energies and 3N/2 hoppings (M = 1024)."""
+    from paper_1705_01387_gb300 import autograd as AG
+    out = {}
+    w = S.config(0)
+    lat = S.build_lattice(w.lattice_args, w.seed)
+    ham = g.gqt_build_hamiltonian(lat, w.energy_scale)
+    phi = torch.empty((lat.n, 1), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, w.seed, 1, phi)
+    dts = np.full(w.n_steps, w.dt)
+    mu = torch.empty((w.n_steps, 1, 1, w.M), dtype=torch.float64, device="cuda")
+    a, b, p, px = (torch.empty_like(phi) for _ in range(4))
+    for graphs in (True, False):
+        g.gqt_set_graphs(ham, graphs)
+        times = []
+        for rep in range(4):
+            g.gqt_vac_init(ham, phi, a, b, 1)
+            g.gqt_msd_init(ham, phi, p, px, 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.gqt_vac_moments(ham, a, b, 1, dts, w.M, mu)
+            g.gqt_msd_moments(ham, p, px, 1, dts, w.M, mu)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        t = min(times[1:])
+        out["c1_graphs" if graphs else "c1_direct"] = {"seconds": t,
+                                                       "us_per_moment": t / (2 * w.n_steps * w.M) * 1e6}
+    w5 = S.config(4)
+    lat5 = S.build_lattice(w5.lattice_args, w5.seed)
+    E = torch.from_numpy(w5.energies).cuda()
+    wts = torch.exp(-E ** 2 / (2 * 0.5 ** 2))
+    topo = AG.BondTopology.from_lattice(lat5)
+    phi5 = torch.empty((lat5.n, 1), dtype=torch.complex128, device="cuda")
+    ham5 = g.gqt_build_hamiltonian(lat5, w5.energy_scale)
+    g.gqt_random_phase(ham5, w5.seed, 1, phi5)
+    spec = AG.VacSigmaLossSpec(topo, w5.energy_scale, phi5, np.full(w5.n_steps - 1, w5.dt), w5.M, E, wts)
+    onsite = torch.from_numpy(lat5.onsite.copy()).requires_grad_(True)
+    hop = torch.full((topo.nbonds,), -2.7, dtype=torch.float64, requires_grad=True)
+    times = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = AG.GqtVacSigmaLoss.apply(onsite, hop, spec)
+        L.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    out["c5_loss_and_grad"] = {"seconds": min(times), "n_orbitals": lat5.n, "n_bonds": topo.nbonds,
+                               "moments": w5.M, "rows": w5.n_steps}
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1705_01387_gb300 as g
@@ -442,10 +496,15 @@ def main():
     ap.add_argument("--fp32-L", type=int, default=0, help="cubic L of the FP32 comparison (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
     ap.add_argument("--precision", action="store_true", help="FP32 vs FP64 per-result error table (C4 workload)")
+    ap.add_argument("--latency", action="store_true", help="latency-bound workloads (C1 graphs on/off, C5 gradient)")
     ap.add_argument("--precision-steps", type=int, default=3, help="VAC/MSD time steps of the error table")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.latency:
+        import torch
+        import paper_1705_01387_gb300 as g
+        print(json.dumps(latency(args, g, torch)))
     elif args.precision:
         import torch
         import paper_1705_01387_gb300 as g

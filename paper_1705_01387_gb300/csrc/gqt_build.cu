@@ -294,6 +294,9 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
     h->length_x = m.length_x;
     h->nseg = nseg;
     h->seg = seg;
+    // FP32 handles run the multi-vector kernels, whose register use fits more
+    // CTAs per SM at 128 threads.
+    h->threads = (precision == GQT_FP64) ? 256 : 128;
     const int64_t n = m.n, K = m.K;
     const bool f64 = precision == GQT_FP64;
     // slot-major device images; hop2 = 2 H / dE, diag2 = 2 U / dE (exact doubling)

@@ -255,11 +255,56 @@ static int rshift_of(int R) {
   return s;
 }
 
+// Resident CTAs per SM of the handle's main moment kernel for R vectors (the
+// kernel the default variant runs), so that the default grid is exactly one
+// wave: SMs x resident CTAs.
+template <bool FP64, bool CH, int KK>
+static int wave_occupancy_k(int R, int variant, int threads) {
+  const void* f = nullptr;
+  if (variant == 2 && R >= 4)
+    f = (const void*)k_cheb_re_wv<FP64, CH, 4, KK>;
+  else if ((variant == 2 && R == 2) || (variant == 3 && R >= 2))
+    f = (const void*)k_cheb_re_wv<FP64, CH, 2, KK>;
+  else if (variant == 2)
+    f = (const void*)k_cheb_re_w<FP64, CH, 2, KK>;
+  else
+    f = (const void*)k_cheb_re_w<FP64, CH, 1, KK>;
+  int n = 0;
+  const size_t smem = (size_t)3 * (threads / 32) * R * sizeof(double2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  return std::max(1, n);
+}
+
+template <bool FP64, bool CH>
+static int wave_occupancy(int K, int R, int variant, int threads) {
+  switch (K) {
+    case 2: return wave_occupancy_k<FP64, CH, 2>(R, variant, threads);
+    case 3: return wave_occupancy_k<FP64, CH, 3>(R, variant, threads);
+    case 4: return wave_occupancy_k<FP64, CH, 4>(R, variant, threads);
+    case 6: return wave_occupancy_k<FP64, CH, 6>(R, variant, threads);
+    default: return 4;
+  }
+}
+
 const BlockTable& gqt_ham::table(int R) {
   auto it = tables.find(R);
   if (it != tables.end()) return *it->second;
   auto t = std::make_unique<BlockTable>();
-  const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 4;
+  int per_sm = blocks_per_sm;
+  if (per_sm <= 0) {
+    if (variant == 0 || threads > 256)
+      per_sm = 4;
+    else if (prec == GQT_FP64)
+      per_sm = hop_real ? wave_occupancy<true, false>(K, R, variant, threads)
+                        : wave_occupancy<true, true>(K, R, variant, threads);
+    else
+      per_sm = hop_real ? wave_occupancy<false, false>(K, R, variant, threads)
+                        : wave_occupancy<false, true>(K, R, variant, threads);
+    per_sm = std::max(4, std::min(per_sm, 8));  // the chunk-ordered kernels (evolution, velocity) want >= 4
+  }
   const int thr = threads;
   const long long max_blocks = (long long)sm_count() * per_sm;
   // at least ~2 elements per thread per CTA
@@ -370,7 +415,10 @@ static bool launch_wave_re(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable&
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_RE(KK)                                                                                          \
-  if (h->variant == 2 && R >= 4)                                                                                 \
+  if (h->variant == 3 && R >= 2)                                                                                 \
+    k_cheb_re_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, l,       \
+                                                                     partial, T.nblocks, slot0, slot_norm, first); \
+  else if (h->variant == 2 && R >= 4)                                                                            \
     k_cheb_re_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, l,       \
                                                                      partial, T.nblocks, slot0, slot_norm, first); \
   else if (h->variant == 2 && R == 2)                                                                            \
@@ -400,7 +448,10 @@ static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_DBL(KK)                                                                                           \
-  if (h->variant == 2 && R >= 4)                                                                                   \
+  if (h->variant == 3 && R >= 2)                                                                                   \
+    k_cheb_dbl_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, partial, \
+                                                                      T.nblocks, m);                              \
+  else if (h->variant == 2 && R >= 4)                                                                              \
     k_cheb_dbl_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \
   else if (h->variant == 2 && R == 2)                                                                              \
@@ -778,7 +829,7 @@ gqt_status gqt_set_graphs(gqt_ham* h, int enable) {
 
 gqt_status gqt_set_variant(gqt_ham* h, int variant) {
   API_BEGIN
-  require(h != nullptr && variant >= 0 && variant <= 2, "gqt_set_variant: variant must be 0, 1 or 2");
+  require(h != nullptr && variant >= 0 && variant <= 3, "gqt_set_variant: variant must be 0, 1, 2 or 3");
   h->variant = variant;
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
   h->graphs.clear();
@@ -1240,7 +1291,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   check_cuda(cudaMemsetAsync(l, 0, vb, st), "memset");
   const int cand_t[] = {128, 256, 512};
   const int cand_b[] = {2, 4, 8};
-  const int cand_v[] = {0, 1, 2};
+  const int cand_v[] = {0, 1, 2, 3};
   const int M = 12;
   DevBuf scratch_mu;
   scratch_mu.ensure((size_t)h->nseg * R * M * sizeof(double));
@@ -1256,6 +1307,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
     for (int t : cand_t)
       for (int b : cand_b) {
         if (v != 0 && t > 256) continue;
+        if (v == 3 && R < 2) continue;
         h->variant = v;
         h->threads = t;
         h->blocks_per_sm = b;
