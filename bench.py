@@ -286,6 +286,98 @@ def latency(args, g, torch):
     return out
 
 
+def paper_examples(args, g, torch):
+    """The paper's two examples (Sec. 5), end to end on one GPU, with the host
+    post-processing of Sec. 2.3.  Ex. 1: square lattice 2000 x 2000, W = 4, hopping
+    -1, dE = 6.1, N_m = 1000, one vector, 20 steps of 0.2, VAC and MSD, energies
+    -6..6 step 0.02.  Ex. 2: chain of 4,000,000 sites, W = 4, dE = 4.1, N_m = 500,
+    two vectors, MSD over the 30 non-uniform steps 0.1..1.0, 1..10, 10..100,
+    energies -4..4 step 0.02.  The paper reports about 3 minutes for both on a
+    Tesla K40 (context only)."""
+    from paper_1705_01387_gb300 import analysis as A
+    out = {}
+
+    def recon(rows, E, dE, nO):
+        r = torch.empty((rows.shape[0], E.numel()), dtype=torch.float64, device="cuda")
+        g.gqt_kpm_reconstruct(rows.contiguous(), E, dE, nO, r)
+        return r
+
+    # Example 1 (diffusive, Fig. 1)
+    t0 = time.perf_counter()
+    ham = g.gqt_build_hamiltonian(None, 6.1, g.GQT_FP64, kind=g.GQT_LATTICE_SQUARE, L1=2000, L2=2000, t=-1.0, W=4.0,
+                                  seed=S.BASE_SEED + 10)
+    nO = ham.n / ham.volume
+    phi = torch.empty((ham.n, 1), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, S.BASE_SEED + 10, 1, phi)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    M, Nt = 1000, 20
+    dts = np.full(Nt, 0.2)
+    E = torch.arange(-300, 301, dtype=torch.float64, device="cuda") * 0.02
+    dos = torch.empty((1, 1, M), dtype=torch.float64, device="cuda")
+    g.gqt_dos_moments(ham, phi, 1, M, dos)
+    a, b = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_vac_init(ham, phi, a, b, 1)
+    vac = torch.empty((Nt, 1, 1, M), dtype=torch.float64, device="cuda")
+    g.gqt_vac_moments(ham, a, b, 1, dts, M, vac)
+    p, px = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_msd_init(ham, phi, p, px, 1)
+    msd = torch.empty((Nt, 1, 1, M), dtype=torch.float64, device="cuda")
+    g.gqt_msd_moments(ham, p, px, 1, dts, M, msd)
+    rd, rv, rm = recon(dos[0], E, 6.1, nO), recon(vac.view(Nt, M), E, 6.1, nO), recon(msd.view(Nt, M), E, 6.1, nO)
+    sv, sm = torch.empty_like(rv), torch.empty_like(rm)
+    g.gqt_sigma_vac(rv, dts, sv)
+    g.gqt_sigma_msd(rm, dts, sm)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rd, rv, sv, sm = rd.cpu().numpy()[0], rv.cpu().numpy(), sv.cpu().numpy(), sm.cpu().numpy()
+    e0 = 300
+    sc = A.semiclassical(rd, rv, sv)
+    # sigma_VAC at t_19 = 3.8 against sigma_MSD at the step midpoint 3.9 (Fig. 1d: equivalent)
+    out["example1_square2000"] = {"build_s": t1 - t0, "compute_s": t2 - t1, "sigma_vac_E0_t3.8": float(sv[-1, e0]),
+                                  "sigma_msd_E0_t3.9": float(sm[-1, e0]), "sigma_sc_E0": float(sc["sigma_sc"][e0]),
+                                  "tau_E0": float(sc["tau"][e0]), "mfp_E0": float(sc["mfp"][e0]),
+                                  "dos_E0": float(rd[e0])}
+    del ham, phi, a, b, p, px
+    torch.cuda.empty_cache()
+    # Example 2 (localized, Fig. 2)
+    t0 = time.perf_counter()
+    ham = g.gqt_build_hamiltonian(None, 4.1, g.GQT_FP64, kind=g.GQT_LATTICE_CHAIN, L1=4_000_000, t=-1.0, W=4.0,
+                                  seed=S.BASE_SEED + 11)
+    nO = ham.n / ham.volume
+    R = 2
+    phi = torch.empty((ham.n, R), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, S.BASE_SEED + 11, R, phi)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    M = 500
+    dts = np.concatenate([np.arange(1, 11) * 0.1, np.arange(1, 11) * 1.0, np.arange(1, 11) * 10.0])
+    Nt = dts.size
+    E = torch.arange(-200, 201, dtype=torch.float64, device="cuda") * 0.02
+    dos = torch.empty((1, R, M), dtype=torch.float64, device="cuda")
+    g.gqt_dos_moments(ham, phi, R, M, dos)
+    p, px = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_msd_init(ham, phi, p, px, R)
+    msd = torch.empty((Nt, 1, R, M), dtype=torch.float64, device="cuda")
+    g.gqt_msd_moments(ham, p, px, R, dts, M, msd)
+    rd = recon(dos[0].mean(0, keepdim=True), E, 4.1, nO)
+    rm = recon(msd[:, 0].mean(1), E, 4.1, nO)
+    sm = torch.empty_like(rm)
+    g.gqt_sigma_msd(rm, dts, sm)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rd, rm, sm = rd.cpu().numpy()[0], rm.cpu().numpy(), sm.cpu().numpy()
+    e0 = 200
+    Lp = A.propagation_length(rd, rm)
+    Lmid = 0.5 * (Lp[1:, e0] + Lp[:-1, e0])
+    out["example2_chain4M"] = {"build_s": t1 - t0, "compute_s": t2 - t1, "xi_saturation_E0": float(A.xi_saturation(Lp)[e0]),
+                               "xi_fit_E0": A.xi_fit(Lmid, sm[1:, e0]), "L_final_E0": float(Lp[-1, e0]),
+                               "max_bessel_orders": int(g.gqt_np_rule(4.1 * 100.0, 4096))}
+    out["total_compute_s"] = out["example1_square2000"]["compute_s"] + out["example2_chain4M"]["compute_s"]
+    out["paper_k40_s_context"] = 180.0
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1705_01387_gb300 as g
@@ -497,10 +589,15 @@ def main():
     ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
     ap.add_argument("--precision", action="store_true", help="FP32 vs FP64 per-result error table (C4 workload)")
     ap.add_argument("--latency", action="store_true", help="latency-bound workloads (C1 graphs on/off, C5 gradient)")
+    ap.add_argument("--paper-examples", action="store_true", help="the paper's two examples (Sec. 5), timed")
     ap.add_argument("--precision-steps", type=int, default=3, help="VAC/MSD time steps of the error table")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.paper_examples:
+        import torch
+        import paper_1705_01387_gb300 as g
+        print(json.dumps(paper_examples(args, g, torch)))
     elif args.latency:
         import torch
         import paper_1705_01387_gb300 as g

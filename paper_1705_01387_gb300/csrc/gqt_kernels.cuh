@@ -1017,11 +1017,11 @@ namespace gqt {
 // elements in flight: all independent loads of the U elements are issued
 // before the dependent neighbour gathers and the arithmetic.
 
-template <bool FP64, bool CH, int U, bool DBL, int KK>
+template <bool FP64, bool CH, int U, bool DBL, int KK, bool first>
 __device__ __forceinline__ void cheb_wave_body(const Ell<FP64, CH>& H, int4 tb, int R, int rs,
                                                const typename Prec<FP64>::V* __restrict__ tm1,
                                                const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
-                                               const typename Prec<FP64>::V* __restrict__ l, int first,
+                                               const typename Prec<FP64>::V* __restrict__ l,
                                                DotAcc<typename Prec<FP64>::V>& d0, DotAcc<typename Prec<FP64>::V>& d1,
                                                DotAcc<typename Prec<FP64>::V>& nl, DotAcc<typename Prec<FP64>::V>& nr) {
   using V = typename Prec<FP64>::V;
@@ -1078,7 +1078,7 @@ __device__ __forceinline__ void cheb_wave_body(const Ell<FP64, CH>& H, int4 tb, 
         if (k < K) nbv[u][k] = __ldg(tm1 + (((size_t)idx[u][k] << rs) + r));
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      V a = cmul_acc(acc[u], dg[u], own[u]);
+      V a = first ? cscale(own[u], dg[u]) : cmul_acc(acc[u], dg[u], own[u]);
 #pragma unroll
       for (int k = 0; k < KMAX; ++k)
         if (k < K) a = cmul_acc(a, hv[u][k], nbv[u][k]);
@@ -1113,7 +1113,12 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_re_w(Ell<FP64, C
   double2* smem = dyn_smem();
   const int b = blockIdx.x;
   DotAcc<V> d0, d1, nl, nr;
-  cheb_wave_body<FP64, CH, U, false, KK>(H, tab[b], R, rs, tm1, tm2, tout, l, first, d0, d1, nl, nr);
+  // the first order (no T_{m-2}) is a separate instantiation of the loop body, so the
+  // other orders fold -T_{m-2} into the first fused multiply-add
+  if (first)
+    cheb_wave_body<FP64, CH, U, false, KK, true>(H, tab[b], R, rs, tm1, tm2, tout, l, d0, d1, nl, nr);
+  else
+    cheb_wave_body<FP64, CH, U, false, KK, false>(H, tab[b], R, rs, tm1, tm2, tout, l, d0, d1, nl, nr);
   if (first) {
     double2 v[3] = {d0.get(), d1.get(), make_double2(nl.get().x, nr.get().x)};
     block_reduce_r<3>(v, R, smem);
@@ -1139,7 +1144,10 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_dbl_w(Ell<FP64, 
   double2* smem = dyn_smem();
   const int b = blockIdx.x;
   DotAcc<V> a0, a1, u0, u1;
-  cheb_wave_body<FP64, CH, U, true, KK>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, m == 1, a0, a1, u0, u1);
+  if (m == 1)
+    cheb_wave_body<FP64, CH, U, true, KK, true>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
+  else
+    cheb_wave_body<FP64, CH, U, true, KK, false>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
   double2 v[2] = {a0.get(), a1.get()};
   block_reduce_r<2>(v, R, smem);
   if ((int)threadIdx.x < R) {
@@ -1218,11 +1226,11 @@ __device__ __forceinline__ void st_v(double2* p, const double2 (&d)[VPT]) {
 
 // One recurrence order for VPT vectors of each site, wavefront order over groups
 // of VPT vectors (gs = log2(R / VPT)).  DBL: l = r doubling dots; otherwise Re <l|.>.
-template <bool FP64, bool CH, int VPT, bool DBL, int KK>
+template <bool FP64, bool CH, int VPT, bool DBL, int KK, bool first>
 __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, int R, int gs,
                                               const typename Prec<FP64>::V* __restrict__ tm1,
                                               const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
-                                              const typename Prec<FP64>::V* __restrict__ l, int first,
+                                              const typename Prec<FP64>::V* __restrict__ l,
                                               DotAcc<typename Prec<FP64>::V> (&d0)[VPT],
                                               DotAcc<typename Prec<FP64>::V> (&d1)[VPT],
                                               DotAcc<typename Prec<FP64>::V> (&nl)[VPT],
@@ -1311,7 +1319,10 @@ __global__ void __launch_bounds__(256, 2) k_cheb_re_wv(Ell<FP64, CH> H, const in
                                                        int slot_norm, int first) {
   using V = typename Prec<FP64>::V;
   DotAcc<V> d0[VPT], d1[VPT], nl[VPT], nr[VPT];
-  cheb_wave_vpt<FP64, CH, VPT, false, KK>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, first, d0, d1, nl, nr);
+  if (first)
+    cheb_wave_vpt<FP64, CH, VPT, false, KK, true>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
+  else
+    cheb_wave_vpt<FP64, CH, VPT, false, KK, false>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
   const int G = 1 << gs;
   if (first) {
     double2 v[3 * VPT];
@@ -1339,7 +1350,10 @@ __global__ void __launch_bounds__(256, 2) k_cheb_dbl_wv(Ell<FP64, CH> H, const i
                                                         double2* __restrict__ partial, int nblocks, int m) {
   using V = typename Prec<FP64>::V;
   DotAcc<V> a0[VPT], a1[VPT], u0[VPT], u1[VPT];
-  cheb_wave_vpt<FP64, CH, VPT, true, KK>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, m == 1, a0, a1, u0, u1);
+  if (m == 1)
+    cheb_wave_vpt<FP64, CH, VPT, true, KK, true>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
+  else
+    cheb_wave_vpt<FP64, CH, VPT, true, KK, false>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
   double2 v[2 * VPT];
 #pragma unroll
   for (int w = 0; w < VPT; ++w) {
