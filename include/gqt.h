@@ -231,6 +231,14 @@ gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
 gqt_status gqt_set_variant(gqt_ham* ham, int variant);
 gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, int* variant, void* stream);
 
+/* Cluster-resident moment rows (default 1): for R = 1 on a single segment, when
+ * a row's two Chebyshev vectors, l and the H~ rows fit in the shared memory of
+ * one thread-block cluster (16 CTAs where the GPU allows, else 8), the whole row
+ * runs as one launch; vectors are exchanged through distributed shared memory
+ * and orders are separated by hardware cluster barriers.  0 keeps the
+ * one-launch-per-order path. */
+gqt_status gqt_set_cluster(gqt_ham* ham, int enable);
+
 /* Use CUDA graphs for repeated loops (default 1). */
 gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
 

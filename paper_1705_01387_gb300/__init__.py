@@ -64,6 +64,7 @@ _SIGS = {
     "gqt_autotune": [_P, _I, _P, _P, _P, _P],
     "gqt_set_graphs": [_P, _I],
     "gqt_set_variant": [_P, _I],
+    "gqt_set_cluster": [_P, _I],
     "gqt_launch_count": [],
     "gqt_profile_start": [],
     "gqt_probe_fp64": [_P, _P],
@@ -338,6 +339,10 @@ def gqt_np_rule(x: float, cap: int = 64) -> int:
 
 def gqt_set_launch(ham: Ham, threads: int = 0, blocks_per_sm: int = 0):
     _check(lib().gqt_set_launch(ham.ptr, int(threads), int(blocks_per_sm)))
+
+
+def gqt_set_cluster(ham: Ham, enable: bool):
+    _check(lib().gqt_set_cluster(ham.ptr, int(bool(enable))))
 
 
 def gqt_set_variant(ham: Ham, variant: int):

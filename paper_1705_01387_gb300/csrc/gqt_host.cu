@@ -24,6 +24,7 @@
 #include "../../include/gqt.h"
 #include "gqt_internal.h"
 #include "gqt_kernels.cuh"
+#include "gqt_cluster.cuh"
 
 using namespace gqt;
 
@@ -474,6 +475,50 @@ static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable
 #undef GQT_WAVE_DBL
 }
 
+// Cluster-resident moment rows (small systems, R = 1, one segment): one launch of
+// k_cheb_cluster per row instead of one launch per order.  Returns false when
+// the row does not fit on chip or clusters are unavailable.
+template <bool FP64, bool CH, bool DBL, class V>
+static bool launch_cluster_row(gqt_ham* h, const Ell<FP64, CH>& H, const V* r, const V* l, double2* partial, int M,
+                               int slot_norm, cudaStream_t st, int* nblk) {
+  if (!h->use_cluster) return false;
+  auto kern = k_cheb_cluster<FP64, CH, DBL>;
+  const int per_site = cluster_site_bytes<FP64, CH>(h->K, !DBL);
+  for (int C : {16, 8}) {
+    const int chunk = (int)((h->n + C - 1) / C);
+    const int thr = std::min(1024, std::max(32, (chunk + 31) / 32 * 32));
+    const size_t smem = (size_t)chunk * per_site + 64 + cluster_red_bytes(M, slot_norm, thr / 32) + 16;
+    if (smem > 220 * 1024) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(thr, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    check_cuda(cudaLaunchKernelEx(&cfg, kern, H, chunk, r, l, partial, M, slot_norm), "k_cheb_cluster");
+    check_launch("k_cheb_cluster");
+    *nblk = C;
+    return true;
+  }
+  return false;
+}
+
 // Launch the moment recursion of r against l and reduce into out, layout
 // [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
 // (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
@@ -486,12 +531,40 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
   void* w1 = h->ws(WS_T1, vb).p;
   void* w2 = h->ws(WS_T2, vb).p;
   const int slots = std::max(M, 2) + 2;
-  double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * nb * R * sizeof(double2)).p;
+  // room for the chunk/wavefront grid and for a 16-CTA cluster row
+  double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * std::max(nb, 16) * R * sizeof(double2)).p;
   const int slot_norm = std::max(M, 2);
   // |mu_m| <= |l||r| (1 + tol): tol 1e-6 for FP64; FP32 storage rounds the vectors, so 1e-3.
   const double tol = (h->prec == GQT_FP64) ? 1e-6 : 1e-3;
   const size_t total = (size_t)h->nseg * R * M;
   const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
+  if (R == 1 && h->nseg == 1 && kind != 0 && h->use_cluster) {
+    int C = 0;
+    bool done = false;
+    DevBuf& cseg = h->ws(WS_CLUSTER_SEG, 4 * sizeof(int));
+    dispatch(h, [&](auto H) {
+      using Tr = EllTraits<decltype(H)>;
+      using V = typename Tr::V;
+      if (kind == 2)
+        done = launch_cluster_row<Tr::fp64, Tr::ch, true>(h, H, (const V*)r, (const V*)nullptr, partial, M, slot_norm,
+                                                          st, &C);
+      else
+        done = launch_cluster_row<Tr::fp64, Tr::ch, false>(h, H, (const V*)r, (const V*)l, partial, M, slot_norm, st,
+                                                           &C);
+    });
+    if (done) {
+      const int segs[2] = {0, C};
+      check_cuda(cudaMemcpyAsync(cseg.p, segs, sizeof segs, cudaMemcpyHostToDevice, st), "cluster table");
+      if (kind == 2)
+        k_reduce_dbl<<<rb, 256, 0, st>>>(partial, M, C, 1, (const int*)cseg.p, 1, 1.0 + tol, (double*)out,
+                                         (int*)h->d_flag.p);
+      else
+        k_reduce<<<rb, 256, 0, st>>>(partial, M, C, 1, (const int*)cseg.p, 1, slot_norm, (1.0 + tol) * (1.0 + tol),
+                                     out, 1, (int*)h->d_flag.p);
+      check_launch("k_reduce(cluster)");
+      return;
+    }
+  }
   const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p},
                                  {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb,
                                   (double)h->variant});
@@ -824,6 +897,13 @@ gqt_status gqt_set_graphs(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_graphs = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_cluster(gqt_ham* h, int enable) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  h->use_cluster = enable != 0;
   API_END
 }
 

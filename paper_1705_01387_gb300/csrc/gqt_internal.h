@@ -55,6 +55,7 @@ enum WorkSlot {
   WS_SMALL0,
   WS_ACC0,      // +0, +1
   WS_E1 = 12,   // +0..+3 evolution Chebyshev buffers
+  WS_CLUSTER_SEG = 17,
   WS_ADJ0 = 20  // adjoint workspace slots start here
 };
 
@@ -82,6 +83,7 @@ struct gqt_ham {
   int blocks_per_sm = 0;
   int variant = 2;  // moment kernels: 0 chunk order, 1 wavefront, 2 wavefront with two elements per thread
   bool use_graphs = true;
+  bool use_cluster = true;  // cluster-resident moment rows for small systems
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

@@ -197,3 +197,37 @@ def test_moment_kernel_variants_agree_with_oracle(variant, name):
     for r in (0, 3):
         ref = h.vac_moments(ph[:, r], np.array([0.5]), [O.np_rule(dE * 0.5, 64)], M)[0]
         assert nerr(vac[0, 0, r], ref) < (1e-10 if prec == g.GQT_FP64 else 1e-4)
+
+
+@pytest.mark.parametrize("name", ["honeycomb32x32", "honeycomb_phases_ragged", "chain", "cubic_fp32"])
+def test_cluster_resident_rows_match_oracle(name):
+    """Small systems run each moment row as one launch on a thread-block cluster
+    (vectors in distributed shared memory); DOS (l = r) and VAC rows equal the
+    oracle's, and equal the per-order path (cluster rows switched off)."""
+    if name == "honeycomb32x32":
+        lat, dE, prec = S.honeycomb(32, 32, -2.7, 1.0, seed=3), S.energy_scale_rule(3, -2.7, 1.0), g.GQT_FP64
+    elif name == "honeycomb_phases_ragged":
+        lat = S.with_random_bond_phases(S.honeycomb(23, 17, -2.7, 2.0, seed=4), 5)
+        dE, prec = S.energy_scale_rule(3, -2.7, 2.0), g.GQT_FP64
+    elif name == "chain":
+        lat, dE, prec = S.chain(9001, -1.0, 4.0, seed=5), 4.2, g.GQT_FP64
+    else:
+        lat, dE, prec = S.cubic(12, -1.0, 16.5, seed=6), S.energy_scale_rule(6, -1.0, 16.5), g.GQT_FP32_ACC64
+    ham = g.gqt_build_hamiltonian(lat, dE, prec)
+    phi = S.random_phase(lat.n, 1, seed=9)
+    cd = torch.complex128 if prec == g.GQT_FP64 else torch.complex64
+    d = torch.from_numpy(phi).to(cd).cuda()
+    M = 257
+    h = O.Hamiltonian(lat, dE)
+    tol = 1e-10 if prec == g.GQT_FP64 else 2e-5
+    Np = [O.np_rule(dE * 0.6, 64)]
+    got = {}
+    for cl in (True, False):
+        g.gqt_set_cluster(ham, cl)
+        mu = np.empty((1, 1, M))
+        g.gqt_dos_moments(ham, d, 1, M, mu)
+        vac = _vac(ham, d, np.array([0.6]), M, Np)
+        got[cl] = (mu.reshape(M), vac.reshape(M))
+        assert nerr(got[cl][0], h.dos_moments(phi[:, 0], M)) < tol
+        assert nerr(got[cl][1], h.vac_moments(phi[:, 0], np.array([0.6]), Np, M)[0]) < (tol if tol < 1e-9 else 1e-4)
+    assert nerr(got[True][0], got[False][0]) < tol and nerr(got[True][1], got[False][1]) < tol
