@@ -99,6 +99,22 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(family: str, n_orbitals: int):
+    """Per-launch DRAM traffic of a moment-kernel family scaled to n_orbitals, from
+    the committed ncu capture; None when the kernel source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_moment_kernels.json")) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, d["kernel_source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != d["kernel_source_sha256"]:
+                return None
+        fam = d["families"][family]
+        return (fam["dram_read_bytes"] + fam["dram_write_bytes"]) / fam["n_orbitals"] * n_orbitals
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload(small: bool, cells: str | None = None, moments: int | None = None):
     """The honeycomb FP64 workload; ``cells`` ('L1xL2') and ``moments`` shrink it for
     profiling captures (the default is the full 4096 x 2048, M = 3000 case)."""
@@ -157,6 +173,28 @@ def fp32_batched(args, g, torch):
         t = e0.elapsed_time(e1) / 2 * 1e-3
         res[prec] = (ham.n * R * M / t, mu[0, 0].cpu().numpy(), t, R, ham.n)
         del phi, ham
+        torch.cuda.empty_cache()
+    # ragged batch: 48 realisations, L ~ U{32..96}, one block-diagonal launch sequence
+    if not args.small and not args.no_ragged:
+        t0 = time.perf_counter()
+        blk = S.ragged_cubic(48, 32, 96, -1.0, 16.5, w.seed)
+        ham = g.gqt_build_hamiltonian(blk, w.energy_scale, g.GQT_FP32_ACC64)
+        t_build = time.perf_counter() - t0
+        phi = torch.empty((ham.n, 1), dtype=torch.complex64, device="cuda")
+        g.gqt_random_phase(ham, w.seed, 1, phi)
+        mu = torch.empty((ham.nseg, 1, M), dtype=torch.float64, device="cuda")
+        g.gqt_dos_moments(ham, phi, 1, M, mu)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.gqt_dos_moments(ham, phi, 1, M, mu)
+        e1.record()
+        torch.cuda.synchronize()
+        tr = e0.elapsed_time(e1) * 1e-3
+        out["ragged"] = {"realisations": int(ham.nseg), "n_orbitals": int(ham.n), "moments": M,
+                         "orbital_moments_per_s": ham.n * M / tr, "ms": tr * 1e3, "build_s": t_build,
+                         "mu0_per_segment_max_dev": float((mu[:, 0, 0] - 1.0).abs().max())}
+        del blk, ham, phi
         torch.cuda.empty_cache()
     v32, mu32, t32, R32, n = res[g.GQT_FP32_ACC64]
     v64, mu64, t64, _, _ = res[g.GQT_FP64]
@@ -475,6 +513,7 @@ def run_ours(args):
                                  "achieved_gbs": N * bpo_k / avg / 1e9 if nl else None,
                                  "share_of_timed_kernels": prof_ms[k] / max(total_prof, 1e-12)}
     kname, bpo = fam[dom]
+    traffic = measured_traffic("k_cheb_re" if dom == 1 else "k_cheb_dbl", N)
     n_launch = int(prof_n[dom])
     avg_s = prof_ms[dom] * 1e-3 / max(n_launch, 1)
     achieved = N * bpo / avg_s / 1e9
@@ -495,13 +534,14 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws} (independent random vectors)"},
         "gpu_launches": int(launches),
         "roofline": ({"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                      "frac": alu_frac, "traffic": None, "kernel": kname, "fp64_fma_per_orbital": fma,
+                      "frac": alu_frac, "traffic": traffic, "kernel": kname, "fp64_fma_per_orbital": fma,
                       "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)",
                       "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
                               "bytes_per_orbital": bpo}}
                      if alu_frac > hbm_frac else
                      {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
-                      "traffic": None, "kernel": kname, "bytes_per_orbital": bpo,
+                      "traffic": traffic, "traffic_source": "profiles/traffic_moment_kernels.json (ncu at N = 4.2M, scaled by N)",
+                      "kernel": kname, "bytes_per_orbital": bpo,
                       "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                       "fp64": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s", "frac": alu_frac,
                                "fp64_fma_per_orbital": fma}}),
@@ -584,6 +624,7 @@ def main():
     ap.add_argument("--moments", type=int, default=None, help="moments per row (profiling captures only)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-fp32", action="store_true", help="skip the batched FP32 vs FP64 comparison")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--fp32-moments", type=int, default=512, help="moments of the FP32/FP64 comparison")
     ap.add_argument("--fp32-L", type=int, default=0, help="cubic L of the FP32 comparison (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
