@@ -208,6 +208,15 @@ gqt_status gqt_vac_loss_grad(gqt_ham* ham, const void* d_phi, const double* dt, 
                              const double* beta, int stride, double* loss, double* d_g_onsite, double* d_g_slot,
                              void* stream);
 
+/* New on-site energies (NULL: zero) and hoppings (hop_im NULL: real) for an
+ * existing handle, row-major [n][max_nb] in the handle's neighbour order, with the
+ * same neighbour list, positions, energy scale and precision.  Validated as in a
+ * build (Hermitian, finite; EINVAL / ENAN) and uploaded into the same device
+ * arrays, so workspace and captured graphs stay valid: repeated evaluations of
+ * a loss at nearby parameters (finite differences, optimisation loops) reuse
+ * them.  A handle built with real hoppings accepts only real ones. */
+gqt_status gqt_update_hamiltonian(gqt_ham* ham, const double* onsite, const double* hop_re, const double* hop_im);
+
 /* Host-side Bessel coefficients J_m(x), m < count (Miller backward recurrence
  * normalised by J_0 + 2 sum J_2k = 1), and the expansion-length rule used when
  * Np <= 0.  x >= 0. */

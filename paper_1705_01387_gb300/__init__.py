@@ -41,6 +41,7 @@ _P, _I, _D, _U64, _I64 = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_int64
 _SIGS = {
     "gqt_build_hamiltonian": [C.POINTER(gqt_lattice), _D, _I, _P, _I, C.POINTER(_P)],
     "gqt_free_hamiltonian": [_P],
+    "gqt_update_hamiltonian": [_P, _P, _P, _P],
     "gqt_generate_lattice": [C.POINTER(gqt_lattice), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "gqt_ham_info": [_P, _P, _P, _P, _P, _P, _P],
     "gqt_random_phase": [_P, _U64, _I, _I, _P, _P],
@@ -190,6 +191,17 @@ def gqt_build_hamiltonian(lattice=None, energy_scale=0.0, precision=GQT_FP64, se
         segp, nseg = seg.ctypes.data, len(seg) - 1
     _check(lib().gqt_build_hamiltonian(C.byref(s), float(energy_scale), int(precision), segp, nseg, C.byref(out)))
     return Ham(out.value, keep)
+
+
+def gqt_update_hamiltonian(ham: Ham, onsite, hop):
+    """New on-site energies [n] and hoppings [n, max_nb] (complex allowed only on complex
+    handles) for an existing handle with the same neighbour list."""
+    on = np.ascontiguousarray(onsite, np.float64)
+    hop = np.asarray(hop)
+    hr = np.ascontiguousarray(np.real(hop), np.float64)
+    hi = np.ascontiguousarray(np.imag(hop), np.float64) if np.iscomplexobj(hop) else None
+    _check(lib().gqt_update_hamiltonian(ham.ptr, on.ctypes.data, hr.ctypes.data,
+                                        None if hi is None else hi.ctypes.data))
 
 
 def gqt_generate_lattice(kind, L1=0, L2=0, L3=0, t=-1.0, W=0.0, vacancy_frac=0.0, seed=0) -> dict:

@@ -19,7 +19,8 @@ import dataclasses
 import numpy as np
 import torch
 
-from . import (GQT_FP64, gqt_build_hamiltonian, gqt_kpm_weights, gqt_np_rule, gqt_vac_loss_grad)
+from . import (GQT_FP64, gqt_build_hamiltonian, gqt_kpm_weights, gqt_np_rule, gqt_update_hamiltonian,
+               gqt_vac_loss_grad)
 
 
 @dataclasses.dataclass
@@ -96,6 +97,8 @@ class VacSigmaLossSpec:
     w: torch.Tensor
     precision: int = GQT_FP64
     stride: int = 0
+    _ham: object = dataclasses.field(default=None, repr=False)  # handle reused across evaluations
+    _beta: object = dataclasses.field(default=None, repr=False)
 
     def beta(self) -> np.ndarray:
         """beta[k][n] = c_k * sum_E w(E) d rhoC_vv(E, t_k)/d mu_n with trapezoid weights c_k."""
@@ -114,8 +117,14 @@ class GqtVacSigmaLoss(torch.autograd.Function):
     def forward(ctx, onsite: torch.Tensor, hop: torch.Tensor, spec: VacSigmaLossSpec):
         lat = spec.topo.lattice(onsite.detach().cpu().numpy().astype(np.float64),
                                 hop.detach().cpu().numpy().astype(np.float64))
-        ham = gqt_build_hamiltonian(lat, spec.energy_scale, spec.precision)
-        beta = spec.beta()
+        if spec._ham is None:
+            spec._ham = gqt_build_hamiltonian(lat, spec.energy_scale, spec.precision)
+        else:  # same topology: update values in place (keeps workspace and CUDA graphs)
+            gqt_update_hamiltonian(spec._ham, lat.onsite, lat.hop)
+        ham = spec._ham
+        if spec._beta is None:
+            spec._beta = spec.beta()
+        beta = spec._beta
         dts = np.concatenate([np.asarray(spec.dt, np.float64), [spec.dt[-1]]])  # Nt = K + 1 rows
         Np = [gqt_np_rule(spec.energy_scale * d, 4096) for d in dts]
         g_on = torch.empty(spec.topo.n, dtype=torch.float64, device=spec.phi.device)

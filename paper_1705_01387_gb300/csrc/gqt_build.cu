@@ -299,6 +299,8 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
     h->threads = (precision == GQT_FP64) ? 256 : 128;
     const int64_t n = m.n, K = m.K;
     const bool f64 = precision == GQT_FP64;
+    h->h_cnt = m.cnt;
+    h->h_idx = m.idx;
     // slot-major device images; hop2 = 2 H / dE, diag2 = 2 U / dE (exact doubling)
     std::vector<int32_t> idx(n * K);
     for (int64_t i = 0; i < n; ++i)
@@ -397,6 +399,84 @@ extern "C" gqt_status gqt_generate_lattice(const gqt_lattice* lattice, int64_t* 
     return e.code;
   } catch (const std::exception& e) {
     set_error(e.what());
+    return GQT_EINVAL;
+  }
+}
+
+
+// New hopping and on-site values for an existing handle (same neighbour list,
+// positions, energy scale and precision): re-validated like a build and uploaded
+// into the same device arrays, so cached graphs and workspace stay valid.
+extern "C" gqt_status gqt_update_hamiltonian(gqt_ham* h, const double* onsite, const double* hop_re,
+                                             const double* hop_im) {
+  try {
+    if (!h || !hop_re) throw Error(GQT_EINVAL, "gqt_update_hamiltonian: null argument");
+    if (h->h_idx.empty()) throw Error(GQT_EINVAL, "gqt_update_hamiltonian: handle has no host topology");
+    const int64_t n = h->n, K = h->K;
+    HostModel m;
+    m.n = n;
+    m.K = (int)K;
+    m.cnt = h->h_cnt;
+    m.idx = h->h_idx;
+    m.hre.assign(hop_re, hop_re + n * K);
+    m.him.assign(n * K, 0.0);
+    if (hop_im) m.him.assign(hop_im, hop_im + n * K);
+    m.eps.assign(n, 0.0);
+    if (onsite) m.eps.assign(onsite, onsite + n);
+    m.dx.assign(n * K, 0.0);  // positions are unchanged; the Hermitian check below ignores dx
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = m.cnt[i]; k < K; ++k) m.hre[i * K + k] = m.him[i * K + k] = 0.0;
+    validate(m, h->seg);
+    bool real = true;
+    for (double v : m.him)
+      if (v != 0.0) real = false;
+    if (real != h->hop_real && !real)
+      throw Error(GQT_EINVAL, "gqt_update_hamiltonian: complex hoppings on a handle built with real ones");
+    const double dE = h->dE;
+    const int hw = h->hop_real ? 1 : 2;
+    auto put = [&](DevBuf& b, const void* src, size_t bytes) {
+      if (bytes > b.bytes) throw Error(GQT_EINVAL, "gqt_update_hamiltonian: size mismatch");
+      check_cuda(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice), "update");
+    };
+    if (h->prec == GQT_FP64) {
+      std::vector<double> hop(n * K * hw), dg(n);
+      for (int64_t i = 0; i < n; ++i) {
+        dg[i] = 2.0 * (m.eps[i] / dE);
+        for (int64_t k = 0; k < K; ++k) {
+          const int64_t s2 = i * K + k, d = k * n + i;
+          if (hw == 1) {
+            hop[d] = 2.0 * (m.hre[s2] / dE);
+          } else {
+            hop[2 * d] = 2.0 * (m.hre[s2] / dE);
+            hop[2 * d + 1] = 2.0 * (m.him[s2] / dE);
+          }
+        }
+      }
+      put(h->d_hop, hop.data(), hop.size() * 8);
+      put(h->d_diag, dg.data(), dg.size() * 8);
+    } else {
+      std::vector<float> hop(n * K * hw), dg(n);
+      for (int64_t i = 0; i < n; ++i) {
+        dg[i] = (float)(2.0 * (m.eps[i] / dE));
+        for (int64_t k = 0; k < K; ++k) {
+          const int64_t s2 = i * K + k, d = k * n + i;
+          if (hw == 1) {
+            hop[d] = (float)(2.0 * (m.hre[s2] / dE));
+          } else {
+            hop[2 * d] = (float)(2.0 * (m.hre[s2] / dE));
+            hop[2 * d + 1] = (float)(2.0 * (m.him[s2] / dE));
+          }
+        }
+      }
+      put(h->d_hop, hop.data(), hop.size() * 4);
+      put(h->d_diag, dg.data(), dg.size() * 4);
+    }
+    return GQT_OK;
+  } catch (const Error& e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_error(std::string("internal error: ") + e.what());
     return GQT_EINVAL;
   }
 }

@@ -172,11 +172,35 @@ static inline void prof_end(size_t i, int cat, cudaStream_t st) {
 // depend on (kind, sizes, pointers, coefficients).  Capture and replay run on
 // the handle's own non-blocking stream, ordered after and before the caller's
 // stream by events, so the caller may pass the legacy default stream.
+// 64-bit digest of a coefficient array (SplitMix64 finaliser folded over the
+// words, so sign patterns cannot cancel); the array itself is stored with the
+// graph and compared exactly on reuse.
+static uint64_t digest(const std::vector<double>& v) {
+  uint64_t x = 0x243F6A8885A308D3ull ^ (uint64_t)v.size();
+  for (double d : v) {
+    uint64_t u;
+    memcpy(&u, &d, 8);
+    x = splitmix_mix(x ^ u) + 0x9E3779B97F4A7C15ull;
+  }
+  return x;
+}
+
 template <class F>
-static void run_graph(gqt_ham* h, const std::string& key, cudaStream_t st, F&& launches) {
+static void run_graph(gqt_ham* h, std::string key, cudaStream_t st, F&& launches,
+                      const std::vector<double>* data = nullptr) {
   if (!h->use_graphs || g_prof.on) {
     launches(st);
     return;
+  }
+  if (data) {
+    char buf[40];
+    snprintf(buf, sizeof buf, "|d%016llx", (unsigned long long)digest(*data));
+    key += buf;
+    auto d = h->graph_data.find(key);
+    if (d != h->graph_data.end() && d->second != *data) {  // digest collision: no graph
+      launches(st);
+      return;
+    }
   }
   if (!h->gstream) {
     check_cuda(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -185,9 +209,10 @@ static void run_graph(gqt_ham* h, const std::string& key, cudaStream_t st, F&& l
   }
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
-    if (h->graphs.size() >= 256) {
+    if (h->graphs.size() >= 512) {
       for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
       h->graphs.clear();
+      h->graph_data.clear();
     }
     cudaGraph_t graph = nullptr;
     check_cuda(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
@@ -205,6 +230,7 @@ static void run_graph(gqt_ham* h, const std::string& key, cudaStream_t st, F&& l
     cudaGraphDestroy(graph);
     check_cuda(e, "cudaGraphInstantiate");
     it = h->graphs.emplace(key, exec).first;
+    if (data) h->graph_data[key] = *data;
   }
   check_cuda(cudaEventRecord(h->gev[0], st), "cudaEventRecord");
   check_cuda(cudaStreamWaitEvent(h->gstream, h->gev[0], 0), "cudaStreamWaitEvent");
@@ -1193,58 +1219,67 @@ void poly_adjoint(gqt_ham* h, const HT& H, const void* r, const void* lam, const
   auto ckp = [&](int j, int q) { return (V*)(ck + ((size_t)2 * j + q) * vb); };
   const double2 z = make_double2(0.0, 0.0);
   const int thr = h->threads;
-  // forward pass: checkpoints (and lbar)
-  check_cuda(cudaMemcpyAsync(ckp(0, 0), r, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
-  if (P > 1) {
-    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], coef[1], 1);
-    check_launch("k_recur(first)");
-    if (1 % s == 1) check_cuda(cudaMemcpyAsync(ckp(0, 1), WA, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
-  } else if (lbar) {
-    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], z, 1);
-    check_launch("k_recur(first)");
+  std::vector<double> cdata(2 * coef.size());
+  for (size_t q = 0; q < coef.size(); ++q) {
+    cdata[2 * q] = coef[q].x;
+    cdata[2 * q + 1] = coef[q].y;
   }
-  const V* um2 = (const V*)r;
-  V* um1 = WA;
-  for (int m = 2; m < P; ++m) {
-    V* out = (m == 2) ? WB : const_cast<V*>(um2);
-    k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, um1, um2, out, lbar, z, coef[m], 0);
-    check_launch("k_recur");
-    if (m % s == 0) check_cuda(cudaMemcpyAsync(ckp(m / s, 0), out, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
-    if (m % s == 1) check_cuda(cudaMemcpyAsync(ckp(m / s, 1), out, vb, cudaMemcpyDeviceToDevice, st), "checkpoint");
-    um2 = um1;
-    um1 = out;
-  }
-  // backward pass
-  check_cuda(cudaMemsetAsync(WA, 0, vb, st), "memset");
-  check_cuda(cudaMemsetAsync(WB, 0, vb, st), "memset");
-  V* X = WA;  // w_{m+1}
-  V* Y = WB;  // w_{m+2} -> w_m
-  for (int j = nck - 1; j >= 0; --j) {
-    const int c = j * s;
-    const int len = std::min(s, P - c);
-    std::vector<const V*> useg(len);
-    for (int q = 0; q < len; ++q) {
-      if (q < 2) {
-        useg[q] = ckp(j, q);
-      } else {
-        V* o = (V*)(seg + (size_t)q * vb);
-        k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, useg[q - 1], useg[q - 2], o, nullptr, z, z, 0);
-        check_launch("k_recur(segment)");
-        useg[q] = o;
+  const std::string key = key_of("padj", {r, lam, rbar, lbar, gdiag, gslot, ck, seg, WA, WB, blk},
+                                 {(double)P, (double)s, (double)thr});
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    // forward pass: checkpoints (and lbar)
+    check_cuda(cudaMemcpyAsync(ckp(0, 0), r, vb, cudaMemcpyDeviceToDevice, s2), "checkpoint");
+    if (P > 1) {
+      k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], coef[1], 1);
+      check_launch("k_recur(first)");
+      if (1 % s == 1) check_cuda(cudaMemcpyAsync(ckp(0, 1), WA, vb, cudaMemcpyDeviceToDevice, s2), "checkpoint");
+    } else if (lbar) {
+      k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, (const V*)r, nullptr, WA, lbar, coef[0], z, 1);
+      check_launch("k_recur(first)");
+    }
+    const V* um2 = (const V*)r;
+    V* um1 = WA;
+    for (int m = 2; m < P; ++m) {
+      V* out = (m == 2) ? WB : const_cast<V*>(um2);
+      k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, um1, um2, out, lbar, z, coef[m], 0);
+      check_launch("k_recur");
+      if (m % s == 0) check_cuda(cudaMemcpyAsync(ckp(m / s, 0), out, vb, cudaMemcpyDeviceToDevice, s2), "checkpoint");
+      if (m % s == 1) check_cuda(cudaMemcpyAsync(ckp(m / s, 1), out, vb, cudaMemcpyDeviceToDevice, s2), "checkpoint");
+      um2 = um1;
+      um1 = out;
+    }
+    // backward pass
+    check_cuda(cudaMemsetAsync(WA, 0, vb, s2), "memset");
+    check_cuda(cudaMemsetAsync(WB, 0, vb, s2), "memset");
+    V* X = WA;  // w_{m+1}
+    V* Y = WB;  // w_{m+2} -> w_m
+    for (int j = nck - 1; j >= 0; --j) {
+      const int c = j * s;
+      const int len = std::min(s, P - c);
+      std::vector<const V*> useg(len);
+      for (int q = 0; q < len; ++q) {
+        if (q < 2) {
+          useg[q] = ckp(j, q);
+        } else {
+          V* o = (V*)(seg + (size_t)q * vb);
+          k_recur<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, useg[q - 1], useg[q - 2], o, nullptr, z, z, 0);
+          check_launch("k_recur(segment)");
+          useg[q] = o;
+        }
+      }
+      for (int m = std::min(c + len, P - 1); m >= c + 1; --m) {
+        const double2 lc = make_double2(coef[m].x, -coef[m].y);
+        const double f = (m == 1 ? 1.0 : 2.0) / h->dE;
+        k_adj_step<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, X, Y, (const V*)lam, lc, useg[m - 1 - c], f, gdiag,
+                                                           gslot);
+        check_launch("k_adj_step");
+        std::swap(X, Y);
       }
     }
-    for (int m = std::min(c + len, P - 1); m >= c + 1; --m) {
-      const double2 lc = make_double2(coef[m].x, -coef[m].y);
-      const double f = (m == 1 ? 1.0 : 2.0) / h->dE;
-      k_adj_step<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, X, Y, (const V*)lam, lc, useg[m - 1 - c], f, gdiag,
-                                                         gslot);
-      check_launch("k_adj_step");
-      std::swap(X, Y);
-    }
-  }
-  const double2 lc0 = make_double2(coef[0].x, -coef[0].y);
-  k_adj_final<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, P > 1 ? X : nullptr, Y, (const V*)lam, lc0, (V*)rbar);
-  check_launch("k_adj_final");
+    const double2 lc0 = make_double2(coef[0].x, -coef[0].y);
+    k_adj_final<Tr::fp64, Tr::ch><<<nb, thr, 0, s2>>>(H, blk, P > 1 ? X : nullptr, Y, (const V*)lam, lc0, (V*)rbar);
+    check_launch("k_adj_final");
+  }, &cdata);
 }
 
 }  // namespace
@@ -1275,7 +1310,7 @@ extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const dou
   double2* LB = (double2*)h->ws(WS_ADJ0 + 10, (size_t)n * sizeof(double2)).p;
   void* tmp = h->ws(WS_ADJ0 + 11, vb).p;
   void* l = h->ws(WS_L, vb).p;
-  double* dpart = (double*)h->ws(WS_ADJ0 + 12, (size_t)nb * sizeof(double)).p;
+  double* dpart = (double*)h->ws(WS_ADJ0 + 12, (size_t)Nt * nb * sizeof(double)).p;  // loss partials per row
   auto Ak = [&](int k) { return (void*)(A + (size_t)k * vb); };
   auto Bk = [&](int k) { return (void*)(B + (size_t)k * vb); };
   // forward states a_k = U(-t_k) phi, b_k = U(-t_k) V phi
@@ -1292,7 +1327,7 @@ extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const dou
   check_cuda(cudaMemsetAsync(gslot, 0, (size_t)n * K * sizeof(double2), st), "memset");
   check_cuda(cudaMemsetAsync(abar, 0, vb, st), "memset");
   check_cuda(cudaMemsetAsync(bbar, 0, vb, st), "memset");
-  std::vector<double> hpart(nb);
+  std::vector<double> hpart((size_t)Nt * nb);
   double total = 0.0;
   dispatch(h, [&](auto H) {
     using Tr = EllTraits<decltype(H)>;
@@ -1313,11 +1348,8 @@ extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const dou
       poly_adjoint(h, H, Bk(k), l, bc, stride, tmp, LB, gdiag, gslot, st);
       k_axpy<V><<<nb, thr, 0, st>>>(blk, (V*)bbar, (const V*)tmp);
       check_launch("k_axpy");
-      k_dot_re<V><<<nb, thr, 0, st>>>(blk, (const V*)l, LB, dpart);
+      k_dot_re<V><<<nb, thr, 0, st>>>(blk, (const V*)l, LB, dpart + (size_t)k * nb);
       check_launch("k_dot_re");
-      check_cuda(cudaMemcpyAsync(hpart.data(), dpart, nb * sizeof(double), cudaMemcpyDeviceToHost, st), "loss");
-      check_cuda(cudaStreamSynchronize(st), "loss");
-      for (int b = 0; b < nb; ++b) total += hpart[b];
       k_vel_adj<Tr::fp64, Tr::ch, double2><<<nb, thr, 0, st>>>(H, blk, LB, (const V*)Ak(k), gslot);
       check_launch("k_vel_adj");
       k_vel_acc<Tr::fp64, Tr::ch><<<nb, thr, 0, st>>>(H, blk, 0.5 * h->dE, LB, (V*)abar);
@@ -1330,6 +1362,10 @@ extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const dou
   k_grad_out<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>((int)n, K, gslot, gdiag,
                                                                             (double2*)d_g_slot, d_g_onsite);
   check_launch("k_grad_out");
+  check_cuda(cudaMemcpyAsync(hpart.data(), dpart, hpart.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "loss");
+  check_cuda(cudaStreamSynchronize(st), "loss");
+  for (int k = Nt - 1; k >= 0; --k)  // the order the rows were summed before: last row first
+    for (int b = 0; b < nb; ++b) total += hpart[(size_t)k * nb + b];
   *loss = total;
   return finish_call(h, st, "gqt_vac_loss_grad");
   API_END

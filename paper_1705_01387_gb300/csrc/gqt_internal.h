@@ -87,6 +87,8 @@ struct gqt_ham {
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, std::vector<double>> graph_data;  // exact data behind hashed graph keys
+  std::vector<int32_t> h_cnt, h_idx;                      // host topology (row-major), for updates
   cudaStream_t gstream = nullptr;  // capture/replay stream of the graphs
   cudaEvent_t gev[2] = {nullptr, nullptr};
 

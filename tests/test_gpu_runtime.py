@@ -231,3 +231,29 @@ def test_cluster_resident_rows_match_oracle(name):
         assert nerr(got[cl][0], h.dos_moments(phi[:, 0], M)) < tol
         assert nerr(got[cl][1], h.vac_moments(phi[:, 0], np.array([0.6]), Np, M)[0]) < (tol if tol < 1e-9 else 1e-4)
     assert nerr(got[True][0], got[False][0]) < tol and nerr(got[True][1], got[False][1]) < tol
+
+
+def test_update_hamiltonian_equals_fresh_build():
+    """New values through gqt_update_hamiltonian give the same moments as a fresh build,
+    and replayed graphs see the new values; a non-Hermitian update is rejected."""
+    lat1 = S.honeycomb(30, 20, -2.7, 1.0, seed=1)
+    lat2 = S.honeycomb(30, 20, -2.7, 2.0, seed=2)
+    lat2.hop[:] *= 1.1
+    dE = S.energy_scale_rule(3, -2.97, 2.0)
+    phi = torch.from_numpy(S.random_phase(lat1.n, 1, seed=3)).cuda()
+    ham = g.gqt_build_hamiltonian(lat1, dE)
+    M = 100
+    mu1 = np.empty((1, 1, M))
+    g.gqt_dos_moments(ham, phi, 1, M, mu1)
+    g.gqt_update_hamiltonian(ham, lat2.onsite, lat2.hop)
+    mu2 = np.empty((1, 1, M))
+    g.gqt_dos_moments(ham, phi, 1, M, mu2)  # same graph key, new H values
+    fresh = g.gqt_build_hamiltonian(lat2, dE)
+    ref = np.empty((1, 1, M))
+    g.gqt_dos_moments(fresh, phi, 1, M, ref)
+    assert np.max(np.abs(mu2 - ref)) < 1e-13 and np.max(np.abs(mu1 - ref)) > 1e-3
+    bad = lat2.hop.copy()
+    bad[5, 1] += 0.3
+    with pytest.raises(g.GqtError) as e:
+        g.gqt_update_hamiltonian(ham, lat2.onsite, bad)
+    assert e.value.status == g.GQT_EINVAL
