@@ -231,10 +231,11 @@ gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
 /* Moment-kernel variant: 0 = each CTA walks one contiguous chunk of sites; 1 =
  * wavefront order (the CTAs of a segment stride through it together, so
  * neighbour gathers hit in L2); 2 = wavefront with more work in flight per
- * thread: two sites per thread for R = 1, and for R >= 2 one site's 2 (R = 2)
- * or 4 (R >= 4) consecutive vectors per thread, sharing one load of its H~ row;
- * 3 = as 2 with 2 vectors per thread for every R >= 2 (fewer registers, more
- * CTAs per SM).  Variants 1-2 cover 2, 3, 4 or 6 neighbour slots and up to 256
+ * thread: two sites per thread for R = 1; for R >= 2 (at most 128 threads per
+ * CTA) consecutive vectors of one site per thread, sharing one load of its H~
+ * row: 4 vectors (R >= 4) in l = r orders, 2 in l != r orders; 3 = as 2 with 2
+ * vectors per thread everywhere.  Unless blocks_per_sm is set, each moment
+ * launch uses exactly as many CTAs as fit on the GPU at once for its kernel.  Variants 1-2 cover 2, 3, 4 or 6 neighbour slots and up to 256
  * threads per CTA; otherwise variant 0 runs.  Default 2.  gqt_autotune also
  * chooses the variant. */
 gqt_status gqt_set_variant(gqt_ham* ham, int variant);

@@ -286,16 +286,26 @@ static int rshift_of(int R) {
 // kernel the default variant runs), so that the default grid is exactly one
 // wave: SMs x resident CTAs.
 template <bool FP64, bool CH, int KK>
-static int wave_occupancy_k(int R, int variant, int threads) {
+static int wave_occupancy_k(int R, int variant, int threads, bool dbl) {
   const void* f = nullptr;
-  if (variant == 2 && R >= 4)
-    f = (const void*)k_cheb_re_wv<FP64, CH, 4, KK>;
-  else if ((variant == 2 && R == 2) || (variant == 3 && R >= 2))
-    f = (const void*)k_cheb_re_wv<FP64, CH, 2, KK>;
-  else if (variant == 2)
-    f = (const void*)k_cheb_re_w<FP64, CH, 2, KK>;
-  else
-    f = (const void*)k_cheb_re_w<FP64, CH, 1, KK>;
+  const bool vpt = threads <= 128 && R >= 2 && (variant == 2 || variant == 3);
+  if (dbl) {
+    if (vpt && variant == 2 && R >= 4)
+      f = (const void*)k_cheb_dbl_wv<FP64, CH, 4, KK>;
+    else if (vpt)
+      f = (const void*)k_cheb_dbl_wv<FP64, CH, 2, KK>;
+    else if (variant == 2)
+      f = (const void*)k_cheb_dbl_w<FP64, CH, 2, KK>;
+    else
+      f = (const void*)k_cheb_dbl_w<FP64, CH, 1, KK>;
+  } else {
+    if (vpt)
+      f = (const void*)k_cheb_re_wv<FP64, CH, 2, KK>;
+    else if (variant == 2)
+      f = (const void*)k_cheb_re_w<FP64, CH, 2, KK>;
+    else
+      f = (const void*)k_cheb_re_w<FP64, CH, 1, KK>;
+  }
   int n = 0;
   const size_t smem = (size_t)3 * (threads / 32) * R * sizeof(double2);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
@@ -306,30 +316,48 @@ static int wave_occupancy_k(int R, int variant, int threads) {
 }
 
 template <bool FP64, bool CH>
-static int wave_occupancy(int K, int R, int variant, int threads) {
+static int wave_occupancy(int K, int R, int variant, int threads, bool dbl) {
   switch (K) {
-    case 2: return wave_occupancy_k<FP64, CH, 2>(R, variant, threads);
-    case 3: return wave_occupancy_k<FP64, CH, 3>(R, variant, threads);
-    case 4: return wave_occupancy_k<FP64, CH, 4>(R, variant, threads);
-    case 6: return wave_occupancy_k<FP64, CH, 6>(R, variant, threads);
+    case 2: return wave_occupancy_k<FP64, CH, 2>(R, variant, threads, dbl);
+    case 3: return wave_occupancy_k<FP64, CH, 3>(R, variant, threads, dbl);
+    case 4: return wave_occupancy_k<FP64, CH, 4>(R, variant, threads, dbl);
+    case 6: return wave_occupancy_k<FP64, CH, 6>(R, variant, threads, dbl);
     default: return 4;
   }
 }
 
-const BlockTable& gqt_ham::table(int R) {
-  auto it = tables.find(R);
+// Resident CTAs per SM of the moment kernel a call of this kind will launch
+// (kind 1: Re <l|T|r> orders, kind 2: l = r orders); 0 when the chunk-ordered
+// kernels run (they use the default table).
+static int moment_grid_per_sm(const gqt_ham* h, int R, int kind) {
+  if (h->blocks_per_sm > 0 || h->variant == 0 || h->threads > 256 || kind == 0) return 0;
+  if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return 0;
+  const bool dbl = kind == 2;
+  int occ;
+  if (h->prec == GQT_FP64)
+    occ = h->hop_real ? wave_occupancy<true, false>(h->K, R, h->variant, h->threads, dbl)
+                      : wave_occupancy<true, true>(h->K, R, h->variant, h->threads, dbl);
+  else
+    occ = h->hop_real ? wave_occupancy<false, false>(h->K, R, h->variant, h->threads, dbl)
+                      : wave_occupancy<false, true>(h->K, R, h->variant, h->threads, dbl);
+  return std::max(1, std::min(occ, 16));
+}
+
+const BlockTable& gqt_ham::table(int R, int grid_per_sm) {
+  const int tkey = R * 64 + grid_per_sm;
+  auto it = tables.find(tkey);
   if (it != tables.end()) return *it->second;
   auto t = std::make_unique<BlockTable>();
-  int per_sm = blocks_per_sm;
+  int per_sm = grid_per_sm > 0 ? grid_per_sm : blocks_per_sm;
   if (per_sm <= 0) {
     if (variant == 0 || threads > 256)
       per_sm = 4;
     else if (prec == GQT_FP64)
-      per_sm = hop_real ? wave_occupancy<true, false>(K, R, variant, threads)
-                        : wave_occupancy<true, true>(K, R, variant, threads);
+      per_sm = hop_real ? wave_occupancy<true, false>(K, R, variant, threads, false)
+                        : wave_occupancy<true, true>(K, R, variant, threads, false);
     else
-      per_sm = hop_real ? wave_occupancy<false, false>(K, R, variant, threads)
-                        : wave_occupancy<false, true>(K, R, variant, threads);
+      per_sm = hop_real ? wave_occupancy<false, false>(K, R, variant, threads, false)
+                        : wave_occupancy<false, true>(K, R, variant, threads, false);
     per_sm = std::max(4, std::min(per_sm, 8));  // the chunk-ordered kernels (evolution, velocity) want >= 4
   }
   const int thr = threads;
@@ -358,7 +386,7 @@ const BlockTable& gqt_ham::table(int R) {
   check_cuda(cudaMemcpy(t->d_blk.p, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice), "table");
   check_cuda(cudaMemcpy(t->d_seg_blk.p, seg_blk.data(), seg_blk.size() * sizeof(int), cudaMemcpyHostToDevice), "table");
   auto& ref = *t;
-  tables[R] = std::move(t);
+  tables[tkey] = std::move(t);
   return ref;
 }
 
@@ -442,13 +470,7 @@ static bool launch_wave_re(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable&
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_RE(KK)                                                                                          \
-  if (h->variant == 3 && R >= 2)                                                                                 \
-    k_cheb_re_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, l,       \
-                                                                     partial, T.nblocks, slot0, slot_norm, first); \
-  else if (h->variant == 2 && R >= 4)                                                                            \
-    k_cheb_re_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, l,       \
-                                                                     partial, T.nblocks, slot0, slot_norm, first); \
-  else if (h->variant == 2 && R == 2)                                                                            \
+  if ((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128)                                       \
     k_cheb_re_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, l,       \
                                                                      partial, T.nblocks, slot0, slot_norm, first); \
   else if (h->variant == 1)                                                                                      \
@@ -475,13 +497,13 @@ static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_DBL(KK)                                                                                           \
-  if (h->variant == 3 && R >= 2)                                                                                   \
+  if (h->variant == 3 && R >= 2 && h->threads <= 128)                                                              \
     k_cheb_dbl_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \
-  else if (h->variant == 2 && R >= 4)                                                                              \
+  else if (h->variant == 2 && R >= 4 && h->threads <= 128)                                                         \
     k_cheb_dbl_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \
-  else if (h->variant == 2 && R == 2)                                                                              \
+  else if (h->variant == 2 && R == 2 && h->threads <= 128)                                                         \
     k_cheb_dbl_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \
   else if (h->variant == 1)                                                                                        \
@@ -551,7 +573,7 @@ static bool launch_cluster_row(gqt_ham* h, const Ell<FP64, CH>& H, const V* r, c
 // (ceil(M/2) recursion steps, double out).
 void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M, void* out, int kind,
                          cudaStream_t st) {
-  const BlockTable& T = h->table(R);
+  const BlockTable& T = h->table(R, moment_grid_per_sm(h, R, kind));
   const int nb = T.nblocks, rs = rshift_of(R);
   const size_t vb = h->vec_bytes(R);
   void* w1 = h->ws(WS_T1, vb).p;

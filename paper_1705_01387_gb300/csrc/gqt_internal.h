@@ -92,7 +92,7 @@ struct gqt_ham {
   cudaStream_t gstream = nullptr;  // capture/replay stream of the graphs
   cudaEvent_t gev[2] = {nullptr, nullptr};
 
-  const gqt::BlockTable& table(int R);
+  const gqt::BlockTable& table(int R, int grid_per_sm = 0);
   gqt::DevBuf& ws(int slot, size_t bytes);
   size_t vec_bytes(int R) const;
   ~gqt_ham();

@@ -1311,7 +1311,7 @@ __device__ __forceinline__ void write_partials_vpt(double2 (&v)[NQ * VPT], int R
 }
 
 template <bool FP64, bool CH, int VPT, int KK>
-__global__ void __launch_bounds__(256, 2) k_cheb_re_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+__global__ void __launch_bounds__(128, 5) k_cheb_re_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
                                                        const typename Prec<FP64>::V* __restrict__ tm1,
                                                        const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
                                                        const typename Prec<FP64>::V* __restrict__ l,
@@ -1344,7 +1344,7 @@ __global__ void __launch_bounds__(256, 2) k_cheb_re_wv(Ell<FP64, CH> H, const in
 }
 
 template <bool FP64, bool CH, int VPT, int KK>
-__global__ void __launch_bounds__(256, 2) k_cheb_dbl_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+__global__ void __launch_bounds__(128, 6) k_cheb_dbl_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
                                                         const typename Prec<FP64>::V* __restrict__ tm1,
                                                         const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
                                                         double2* __restrict__ partial, int nblocks, int m) {
