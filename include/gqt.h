@@ -187,6 +187,24 @@ gqt_status gqt_kpm_reconstruct(const double* d_mu, int rows, int M, const double
 gqt_status gqt_kpm_weights(int M, const double* d_E, int NE, const double* d_w, double energy_scale,
                            double n_over_omega, int kernel, double* d_beta, void* stream);
 
+/* Moment weights of the loss L = sum_e w[e] sigma_VAC(E_e, t_K) over K+1 VAC rows at
+ * t_0 = 0 .. t_K (dt: host [K]): sigma_VAC(t_K) is the trapezoid sum
+ * sum_k c_k rho C_vv(t_k) (Eq. 2) with c_0 = dt_0/2, c_k = (dt_{k-1} + dt_k)/2,
+ * c_K = dt_{K-1}/2, and rho C_vv is linear in the moments (gqt_kpm_weights), so
+ * d_beta[k][n] = c_k * kw[n] (device FP64 [K+1][M]); feed it to gqt_vac_loss_grad. */
+gqt_status gqt_sigma_vac_loss_weights(int M, const double* d_E, int NE, const double* d_w, double energy_scale,
+                                      double n_over_omega, int kernel, const double* dt, int K, double* d_beta,
+                                      void* stream);
+
+/* Gradients of real (and imaginary) bond hoppings from the slot gradients of
+ * gqt_vac_loss_grad (d_g_slot: device FP64 [n_slots][2], n_slots = n * max_nb):
+ * bond b is the Hermitian pair of slots d_slot_a[b] and d_slot_b[b] (flat indices
+ * i*max_nb + k, device int64); d_g_re[b] = Re(G_a + G_b), d_g_im[b] (may be NULL)
+ * = Im(G_a) - Im(G_b).  A slot index outside [0, n_slots) is not read: that bond's
+ * outputs are NaN.  Stream-ordered, asynchronous. */
+gqt_status gqt_bond_gradients(const double* d_g_slot, long long n_slots, const long long* d_slot_a,
+                              const long long* d_slot_b, int nbonds, double* d_g_re, double* d_g_im, void* stream);
+
 /* Running conductivity from the VAC (Eq. 2): sigma[k][e] = sum_{j<k} dt[j] (v[j][e] + v[j+1][e]) / 2
  * over rows at t_0 = 0 .. t_{Nt-1} of rho*C_vv (device [Nt][NE]); dt host [Nt]. */
 gqt_status gqt_sigma_vac(const double* d_vac, const double* dt, int Nt, int NE, double* d_sigma, void* stream);
@@ -203,7 +221,7 @@ gqt_status gqt_sigma_msd(const double* d_msd, const double* dt, int Nt, int NE, 
  * dJ = Re sum conj(G_ik) dH_{i,idx(i,k)} over slots, every slot independent
  * (a real bond's hopping t_ij has dJ/dt = Re(G_ij + G_ji)).  *loss receives J.
  * Intermediate Chebyshev vectors are recomputed from checkpoints taken every
- * `stride` orders (stride <= 0: ceil(sqrt(M))). */
+ * `stride` orders (stride <= 0: ceil(sqrt(M))).  beta may be host or device memory. */
 gqt_status gqt_vac_loss_grad(gqt_ham* ham, const void* d_phi, const double* dt, const int* Np, int Nt, int M,
                              const double* beta, int stride, double* loss, double* d_g_onsite, double* d_g_slot,
                              void* stream);

@@ -56,6 +56,8 @@ _SIGS = {
     "gqt_msd_moments": [_P, _P, _P, _I, _P, _P, _I, _I, _P, _P],
     "gqt_kpm_reconstruct": [_P, _I, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kpm_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _P],
+    "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
+    "gqt_bond_gradients": [_P, _I64, _P, _P, _I, _P, _P, _P],
     "gqt_sigma_vac": [_P, _P, _I, _I, _P, _P],
     "gqt_sigma_msd": [_P, _P, _I, _I, _P, _P],
     "gqt_vac_loss_grad": [_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P],
@@ -313,6 +315,25 @@ def gqt_kpm_weights(M: int, E, w, energy_scale: float, n_over_omega: float, beta
     return beta
 
 
+def gqt_sigma_vac_loss_weights(M: int, E, w, energy_scale: float, n_over_omega: float, dt, beta, kernel: int = 0,
+                               stream=None):
+    """beta [K+1, M] (CUDA float64) of L = sum_E w(E) sigma_VAC(E, t_K) over rows t_0..t_K (dt: K steps)."""
+    dt = np.ascontiguousarray(np.atleast_1d(dt), np.float64)
+    _check(lib().gqt_sigma_vac_loss_weights(int(M), _dptr(E, "E"), int(E.numel()), _dptr(w, "w"),
+                                            float(energy_scale), float(n_over_omega), int(kernel), dt.ctypes.data,
+                                            int(dt.size), _dptr(beta, "beta"), _stream(stream)))
+    return beta
+
+
+def gqt_bond_gradients(g_slot, slot_a, slot_b, g_re, g_im=None, stream=None):
+    """g_slot: CUDA float64 [n, K, 2]; slot_a/slot_b: CUDA int64 [nbonds]; g_re (g_im): CUDA float64 [nbonds]."""
+    _check(lib().gqt_bond_gradients(_dptr(g_slot, "g_slot"), int(g_slot.numel() // 2), _dptr(slot_a, "slot_a"),
+                                    _dptr(slot_b, "slot_b"),
+                                    int(slot_a.numel()), _dptr(g_re, "g_re"),
+                                    None if g_im is None else _dptr(g_im, "g_im"), _stream(stream)))
+    return g_re
+
+
 def gqt_sigma_vac(vac, dt, out, stream=None):
     dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (vac.shape[0],)))
     _check(lib().gqt_sigma_vac(_dptr(vac, "vac"), dt.ctypes.data, int(vac.shape[0]), int(vac.shape[1]),
@@ -328,12 +349,18 @@ def gqt_sigma_msd(msd, dt, out, stream=None):
 
 
 def gqt_vac_loss_grad(ham: Ham, phi, dt, M: int, beta, g_onsite, g_slot, Np=None, stride: int = 0, stream=None):
-    """beta: numpy [Nt, M]; g_onsite: CUDA float64 [n]; g_slot: CUDA float64 [n, K, 2]. Returns the loss."""
+    """beta: [Nt, M] numpy or CUDA float64; g_onsite: CUDA float64 [n]; g_slot: CUDA float64 [n, K, 2].
+    Returns the loss."""
     dt, npp = _steps(dt, Np)
-    beta = np.ascontiguousarray(beta, np.float64)
+    import torch
+    if isinstance(beta, torch.Tensor):
+        bptr = _dptr(beta, "beta")
+    else:
+        beta = np.ascontiguousarray(beta, np.float64)
+        bptr = beta.ctypes.data
     loss = C.c_double()
     _check(lib().gqt_vac_loss_grad(ham.ptr, _dptr(phi, "phi"), dt.ctypes.data,
-                                   None if npp is None else npp.ctypes.data, dt.size, int(M), beta.ctypes.data,
+                                   None if npp is None else npp.ctypes.data, dt.size, int(M), bptr,
                                    int(stride), C.byref(loss), _dptr(g_onsite, "g_onsite"), _dptr(g_slot, "g_slot"),
                                    _stream(stream)))
     return loss.value

@@ -9,8 +9,8 @@ library's hand-written adjoint (gqt_vac_loss_grad: reverse three-term recurrence
 with sqrt(M) checkpointing).  The energy scale dE is held fixed.
 
 Glue only: Hamiltonian assembly from (onsite, hop) is index bookkeeping on the
-host, the moment weights come from gqt_kpm_weights, and loss and gradients from
-gqt_vac_loss_grad.
+host; the moment weights come from gqt_sigma_vac_loss_weights, loss and slot
+gradients from gqt_vac_loss_grad and bond gradients from gqt_bond_gradients.
 """
 from __future__ import annotations
 
@@ -19,8 +19,8 @@ import dataclasses
 import numpy as np
 import torch
 
-from . import (GQT_FP64, gqt_build_hamiltonian, gqt_kpm_weights, gqt_np_rule, gqt_update_hamiltonian,
-               gqt_vac_loss_grad)
+from . import (GQT_FP64, gqt_bond_gradients, gqt_build_hamiltonian, gqt_np_rule, gqt_sigma_vac_loss_weights,
+               gqt_update_hamiltonian, gqt_vac_loss_grad)
 
 
 @dataclasses.dataclass
@@ -100,16 +100,12 @@ class VacSigmaLossSpec:
     _ham: object = dataclasses.field(default=None, repr=False)  # handle reused across evaluations
     _beta: object = dataclasses.field(default=None, repr=False)
 
-    def beta(self) -> np.ndarray:
-        """beta[k][n] = c_k * sum_E w(E) d rhoC_vv(E, t_k)/d mu_n with trapezoid weights c_k."""
-        kw = torch.empty(self.M, dtype=torch.float64, device=self.E.device)
-        gqt_kpm_weights(self.M, self.E, self.w, self.energy_scale, self.topo.n / self.topo.volume, kw)
+    def beta(self):
+        """beta[k][n] = c_k * sum_E w(E) d rhoC_vv(E, t_k)/d mu_n (trapezoid weights c_k), on the device."""
         dt = np.asarray(self.dt, np.float64)
-        K = dt.size
-        c = np.zeros(K + 1)
-        c[:-1] += 0.5 * dt
-        c[1:] += 0.5 * dt
-        return np.outer(c, kw.cpu().numpy())
+        b = torch.empty((dt.size + 1, self.M), dtype=torch.float64, device=self.E.device)
+        return gqt_sigma_vac_loss_weights(self.M, self.E, self.w, self.energy_scale, self.topo.n / self.topo.volume,
+                                          dt, b)
 
 
 class GqtVacSigmaLoss(torch.autograd.Function):
@@ -130,10 +126,11 @@ class GqtVacSigmaLoss(torch.autograd.Function):
         g_on = torch.empty(spec.topo.n, dtype=torch.float64, device=spec.phi.device)
         g_slot = torch.empty((spec.topo.n, spec.topo.K, 2), dtype=torch.float64, device=spec.phi.device)
         loss = gqt_vac_loss_grad(ham, spec.phi, dts, spec.M, beta, g_on, g_slot, Np=Np, stride=spec.stride)
-        gs = g_slot[..., 0].reshape(-1)
-        ia = torch.from_numpy(spec.topo.slot_a).to(gs.device)
-        ib = torch.from_numpy(spec.topo.slot_b).to(gs.device)
-        g_hop = gs[ia] + gs[ib]
+        ia = torch.from_numpy(spec.topo.slot_a).to(g_slot.device)
+        ib = torch.from_numpy(spec.topo.slot_b).to(g_slot.device)
+        g_hop = torch.empty(spec.topo.nbonds, dtype=torch.float64, device=g_slot.device)
+        gqt_bond_gradients(g_slot, ia, ib, g_hop)
+        torch.cuda.synchronize(g_slot.device)
         ctx.save_for_backward(g_on.to(onsite.device), g_hop.to(hop.device))
         return torch.tensor(loss, dtype=torch.float64, device=onsite.device)
 

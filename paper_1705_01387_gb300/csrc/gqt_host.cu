@@ -1323,6 +1323,12 @@ extern "C" gqt_status gqt_vac_loss_grad(gqt_ham* h, const void* d_phi, const dou
   const int* blk = (const int*)T.d_blk.p;
   const int thr = h->threads;
   if (stride <= 0) stride = (int)std::ceil(std::sqrt((double)M));
+  std::vector<double> hbeta;
+  if (!is_host_ptr(beta)) {  // device weights: one copy to the host (they become kernel arguments)
+    hbeta.resize((size_t)Nt * M);
+    check_cuda(cudaMemcpy(hbeta.data(), beta, hbeta.size() * sizeof(double), cudaMemcpyDeviceToHost), "beta");
+    beta = hbeta.data();
+  }
   char* A = (char*)h->ws(WS_ADJ0 + 4, (size_t)Nt * vb).p;
   char* B = (char*)h->ws(WS_ADJ0 + 5, (size_t)Nt * vb).p;
   double* gdiag = (double*)h->ws(WS_ADJ0 + 6, (size_t)n * sizeof(double)).p;
@@ -1514,5 +1520,51 @@ extern "C" gqt_status gqt_probe_fp64(double* gflops, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *gflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e9;
+  API_END
+}
+
+// Moment weights of the loss L = sum_e w[e] sigma_VAC(E_e, t_K): sigma_VAC at the
+// last of the K+1 rows t_0 .. t_K is the trapezoid sum sum_k c_k rho C_vv(t_k)
+// (Eq. 2; c_0 = dt_0/2, c_k = (dt_{k-1} + dt_k)/2, c_K = dt_{K-1}/2), and each
+// rho C_vv is linear in the moments (gqt_kpm_weights), so beta[k][n] = c_k kw[n].
+extern "C" gqt_status gqt_sigma_vac_loss_weights(int M, const double* d_E, int NE, const double* d_w,
+                                                 double energy_scale, double n_over_omega, int kernel,
+                                                 const double* dt, int K, double* d_beta, void* stream) {
+  API_BEGIN
+  require(d_beta && dt && K >= 1 && M >= 1, "gqt_sigma_vac_loss_weights: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> c(K + 1, 0.0);
+  for (int k = 0; k < K; ++k) {
+    require(std::isfinite(dt[k]) && dt[k] > 0, "time steps must be positive");
+    c[k] += 0.5 * dt[k];
+    c[k + 1] += 0.5 * dt[k];
+  }
+  double* buf = nullptr;
+  check_cuda(cudaMallocAsync((void**)&buf, (size_t)(M + K + 1) * sizeof(double), st), "cudaMallocAsync");
+  check_cuda(cudaMemcpyAsync(buf + M, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, st), "copy");
+  gqt_status s = gqt_kpm_weights(M, d_E, NE, d_w, energy_scale, n_over_omega, kernel, buf, stream);
+  if (s != GQT_OK) {
+    cudaFreeAsync(buf, st);
+    return s;
+  }
+  const size_t total = (size_t)(K + 1) * M;
+  k_trapezoid_outer<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, st>>>(buf + M, K + 1, buf, M, d_beta);
+  check_launch("k_trapezoid_outer");
+  check_cuda(cudaFreeAsync(buf, st), "cudaFreeAsync");
+  check_cuda(cudaStreamSynchronize(st), "gqt_sigma_vac_loss_weights");
+  API_END
+}
+
+extern "C" gqt_status gqt_bond_gradients(const double* d_g_slot, long long n_slots, const long long* d_slot_a,
+                                         const long long* d_slot_b, int nbonds, double* d_g_re, double* d_g_im,
+                                         void* stream) {
+  API_BEGIN
+  require(d_g_slot && d_slot_a && d_slot_b && d_g_re && nbonds >= 0 && n_slots >= 0,
+          "gqt_bond_gradients: bad argument");
+  if (nbonds == 0) return GQT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_bond_grad<<<(int)std::min(4096, (nbonds + 255) / 256), 256, 0, st>>>((const double2*)d_g_slot, n_slots, d_slot_a,
+                                                                          d_slot_b, nbonds, d_g_re, d_g_im);
+  check_launch("k_bond_grad");
   API_END
 }

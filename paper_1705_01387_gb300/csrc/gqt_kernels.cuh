@@ -1365,3 +1365,32 @@ __global__ void __launch_bounds__(128, 6) k_cheb_dbl_wv(Ell<FP64, CH> H, const i
 }
 
 }  // namespace gqt
+
+namespace gqt {
+// Bond gradients from slot gradients: bond b joins slots sa[b] and sb[b] (the two
+// directions of one Hermitian pair); for the real and imaginary part of its
+// hopping, dJ/dRe = Re(G_a + G_b) and dJ/dIm = Im(G_a) - Im(G_b).
+static __global__ void k_bond_grad(const double2* __restrict__ gslot, long long n_slots,
+                                   const long long* __restrict__ sa, const long long* __restrict__ sb, int nbonds,
+                                   double* __restrict__ g_re, double* __restrict__ g_im) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbonds; b += gridDim.x * blockDim.x) {
+    const long long ia = sa[b], ib = sb[b];
+    if (ia < 0 || ia >= n_slots || ib < 0 || ib >= n_slots) {
+      g_re[b] = CUDART_NAN;
+      if (g_im) g_im[b] = CUDART_NAN;
+      continue;
+    }
+    const double2 a = gslot[ia], c = gslot[ib];
+    g_re[b] = a.x + c.x;
+    if (g_im) g_im[b] = a.y - c.y;
+  }
+}
+
+// beta[k][n] = c_k * kw[n] with trapezoid weights c_k of sigma_VAC at the last row.
+static __global__ void k_trapezoid_outer(const double* __restrict__ c, int rows, const double* __restrict__ kw, int M,
+                                         double* __restrict__ beta) {
+  const size_t total = (size_t)rows * M;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
+    beta[t] = c[t / M] * kw[t % M];
+}
+}  // namespace gqt

@@ -134,3 +134,45 @@ def test_differentiation_workload_full_size():
                 vals.append(float(AG.GqtVacSigmaLoss.apply(*args, spec)))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - float(grad[q])) <= 1e-4 * gmax
+
+
+def test_sigma_vac_loss_weights_linear_form():
+    """beta of gqt_sigma_vac_loss_weights turns moments into the loss: for any moments
+    mu [K+1][M], sum beta*mu equals sum_E w(E) sigma_VAC(E, t_K) from the oracle's KPM
+    reconstruction (Eqs. 26, 31) and trapezoid rule (Eq. 2), with unequal steps."""
+    K, M, dE, n_over_omega = 4, 57, 9.3, 0.37
+    rng = np.random.default_rng(5)
+    mu = rng.standard_normal((K + 1, M)) / (1 + np.arange(M))
+    dt = np.array([0.3, 0.7, 0.45, 1.1])
+    E = np.linspace(-0.9 * dE, 0.85 * dE, 23)
+    w = rng.standard_normal(E.size)
+    beta = torch.empty((K + 1, M), dtype=torch.float64, device="cuda")
+    g.gqt_sigma_vac_loss_weights(M, torch.from_numpy(E).cuda(), torch.from_numpy(w).cuda(), dE, n_over_omega, dt,
+                                 beta)
+    got = float(np.sum(beta.cpu().numpy() * mu))
+    sig = O.sigma_vac(O.kpm_reconstruct(mu, E, dE, n_over_omega), np.concatenate([dt, [0.0]]))
+    want = float(np.sum(w * sig[-1]))
+    assert abs(got - want) <= 1e-12 * max(abs(want), float(np.sum(np.abs(w * sig[-1]))))
+
+
+def test_bond_gradients_gather():
+    """Bond gradients are the Hermitian-pair sums of slot gradients; an index outside the
+    slot array gives NaN for that bond and leaves the others alone."""
+    lat = S.with_random_bond_phases(S.honeycomb(6, 4, -2.7, 2.0, seed=2), 3)
+    topo = AG.BondTopology.from_lattice(lat)
+    rng = np.random.default_rng(8)
+    gs = rng.standard_normal((lat.n, lat.max_nb, 2))
+    ia, ib = topo.slot_a.copy(), topo.slot_b.copy()
+    ia[5] = lat.n * lat.max_nb  # one past the end
+    ib[9] = -1
+    gre = torch.empty(topo.nbonds, dtype=torch.float64, device="cuda")
+    gim = torch.empty_like(gre)
+    g.gqt_bond_gradients(torch.from_numpy(gs).cuda(), torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda(), gre,
+                         gim)
+    gre, gim = gre.cpu().numpy(), gim.cpu().numpy()
+    flat = gs.reshape(-1, 2)
+    ok = np.ones(topo.nbonds, bool)
+    ok[[5, 9]] = False
+    assert np.isnan(gre[~ok]).all() and np.isnan(gim[~ok]).all()
+    assert np.array_equal(gre[ok], (flat[ia[ok], 0] + flat[ib[ok], 0]))
+    assert np.array_equal(gim[ok], (flat[ia[ok], 1] - flat[ib[ok], 1]))
