@@ -282,6 +282,15 @@ static int rshift_of(int R) {
   return s;
 }
 
+// Next-iteration prefetch of the multi-vector kernels (FP32 storage, where the
+// dependent index load bounds the iteration): needs a lane group of at least K + 1
+// lanes per site within one warp.
+template <bool FP64>
+static bool vpt_prefetch(int KK, int R, int vpt) {
+  const int G = R / vpt;
+  return !FP64 && G >= KK + 1 && G <= 32;
+}
+
 // Resident CTAs per SM of the handle's main moment kernel for R vectors (the
 // kernel the default variant runs), so that the default grid is exactly one
 // wave: SMs x resident CTAs.
@@ -291,16 +300,19 @@ static int wave_occupancy_k(int R, int variant, int threads, bool dbl) {
   const bool vpt = threads <= 128 && R >= 2 && (variant == 2 || variant == 3);
   if (dbl) {
     if (vpt && variant == 2 && R >= 4)
-      f = (const void*)k_cheb_dbl_wv<FP64, CH, 4, KK>;
+      f = vpt_prefetch<FP64>(KK, R, 4) ? (const void*)k_cheb_dbl_wv<FP64, CH, 4, KK, !FP64>
+                                       : (const void*)k_cheb_dbl_wv<FP64, CH, 4, KK>;
     else if (vpt)
-      f = (const void*)k_cheb_dbl_wv<FP64, CH, 2, KK>;
+      f = vpt_prefetch<FP64>(KK, R, 2) ? (const void*)k_cheb_dbl_wv<FP64, CH, 2, KK, !FP64>
+                                       : (const void*)k_cheb_dbl_wv<FP64, CH, 2, KK>;
     else if (variant == 2)
       f = (const void*)k_cheb_dbl_w<FP64, CH, 2, KK>;
     else
       f = (const void*)k_cheb_dbl_w<FP64, CH, 1, KK>;
   } else {
     if (vpt)
-      f = (const void*)k_cheb_re_wv<FP64, CH, 2, KK>;
+      f = vpt_prefetch<FP64>(KK, R, 2) ? (const void*)k_cheb_re_wv<FP64, CH, 2, KK, !FP64>
+                                       : (const void*)k_cheb_re_wv<FP64, CH, 2, KK>;
     else if (variant == 2)
       f = (const void*)k_cheb_re_w<FP64, CH, 2, KK>;
     else
@@ -470,7 +482,10 @@ static bool launch_wave_re(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable&
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_RE(KK)                                                                                          \
-  if ((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128)                                       \
+  if ((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128 && vpt_prefetch<FP64>(KK, R, 2))    \
+    k_cheb_re_wv<FP64, CH, 2, KK, !FP64><<<T.nblocks, h->threads, sm, st>>>(                                     \
+        H, tab, R, rs - 1, tm1, tm2, tout, l, partial, T.nblocks, slot0, slot_norm, first);                      \
+  else if ((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128)                                  \
     k_cheb_re_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, l,       \
                                                                      partial, T.nblocks, slot0, slot_norm, first); \
   else if (h->variant == 1)                                                                                      \
@@ -497,9 +512,15 @@ static bool launch_wave_dbl(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_WAVE_DBL(KK)                                                                                           \
-  if (h->variant == 3 && R >= 2 && h->threads <= 128)                                                              \
+  if (h->variant == 3 && R >= 2 && h->threads <= 128 && vpt_prefetch<FP64>(KK, R, 2))                            \
+    k_cheb_dbl_wv<FP64, CH, 2, KK, !FP64><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout,   \
+                                                                             partial, T.nblocks, m);             \
+  else if (h->variant == 3 && R >= 2 && h->threads <= 128)                                                         \
     k_cheb_dbl_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \
+  else if (h->variant == 2 && R >= 4 && h->threads <= 128 && vpt_prefetch<FP64>(KK, R, 4))                       \
+    k_cheb_dbl_wv<FP64, CH, 4, KK, !FP64><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout,   \
+                                                                             partial, T.nblocks, m);             \
   else if (h->variant == 2 && R >= 4 && h->threads <= 128)                                                         \
     k_cheb_dbl_wv<FP64, CH, 4, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 2, tm1, tm2, tout, partial, \
                                                                       T.nblocks, m);                              \

@@ -1226,7 +1226,36 @@ __device__ __forceinline__ void st_v(double2* p, const double2 (&d)[VPT]) {
 
 // One recurrence order for VPT vectors of each site, wavefront order over groups
 // of VPT vectors (gs = log2(R / VPT)).  DBL: l = r doubling dots; otherwise Re <l|.>.
-template <bool FP64, bool CH, int VPT, bool DBL, int KK, bool first>
+// Lane shuffles of the hopping types (a 64-bit or two-component value moves in parts).
+__device__ __forceinline__ float shfl_g(float v, int src, int w) { return __shfl_sync(0xffffffffu, v, src, w); }
+__device__ __forceinline__ double shfl_g(double v, int src, int w) { return __shfl_sync(0xffffffffu, v, src, w); }
+__device__ __forceinline__ float2 shfl_g(float2 v, int src, int w) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src, w), __shfl_sync(0xffffffffu, v.y, src, w));
+}
+__device__ __forceinline__ double2 shfl_g(double2 v, int src, int w) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src, w), __shfl_sync(0xffffffffu, v.y, src, w));
+}
+template <class S>
+__device__ __forceinline__ void put_re(S& h, S v) { h = v; }
+__device__ __forceinline__ void put_re(float2& h, float v) { h.x = v; }
+__device__ __forceinline__ void put_re(double2& h, double v) { h.x = v; }
+template <class S>
+__device__ __forceinline__ S get_re(S h) { return h; }
+__device__ __forceinline__ float get_re(float2 h) { return h.x; }
+__device__ __forceinline__ double get_re(double2 h) { return h.x; }
+
+// One CTA's share of a wavefront segment with VPT vectors per thread: G = R/VPT
+// consecutive lanes (gs = log2 G) serve one site, each lane its VPT vectors.  The
+// loop runs over block-uniform offsets g0, so every lane of the block takes the same
+// trip count (lanes past the segment end skip the work, not the loop).
+//
+// PF (requires KK + 1 <= G <= 32): the site's K indices, K hoppings and diagonal are
+// fetched one iteration ahead, one item per lane of the G-lane group (slot g for
+// lane g < K, the diagonal for lane K), while the current iteration's neighbour
+// loads are in flight; the group then shares them by shuffles.  This takes the
+// dependent index load off the iteration's critical path (index -> neighbour
+// vector), which is what bounds the FP32 multi-vector form.
+template <bool FP64, bool CH, int VPT, bool DBL, int KK, bool first, bool PF>
 __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, int R, int gs,
                                               const typename Prec<FP64>::V* __restrict__ tm1,
                                               const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
@@ -1237,23 +1266,58 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
                                               DotAcc<typename Prec<FP64>::V> (&nr)[VPT]) {
   using V = typename Prec<FP64>::V;
   using S = typename Prec<FP64>::S;
+  using HT = typename Ell<FP64, CH>::HT;
   const size_t gb = (size_t)tb.x << gs, ge = (size_t)tb.y << gs;
   const size_t step = (size_t)tb.w * blockDim.x;
   const int gmask = (1 << gs) - 1;
-  for (size_t gi = gb + (size_t)tb.z * blockDim.x + threadIdx.x; gi < ge; gi += step) {
+  const int G = 1 << gs;
+  const int lg = (int)threadIdx.x & gmask;
+  int pidx = 0;
+  HT phop{};
+  auto fetch_next = [&](size_t gn) {
+    if (gn < ge) {
+      const int i = (int)(gn >> gs);
+      if (lg < KK) {
+        const size_t s = (size_t)lg * H.n + i;
+        pidx = __ldg(H.idx + s);
+        phop = __ldg(H.hop2 + s);
+      } else if (lg == KK) {
+        put_re(phop, __ldg(H.diag2 + i));
+      }
+    }
+  };
+  const size_t g_first = gb + (size_t)tb.z * blockDim.x;
+  if (PF) fetch_next(g_first + threadIdx.x);
+  for (size_t g0 = g_first; g0 < ge; g0 += step) {
+    const size_t gi = g0 + threadIdx.x;
+    int idx[KK];
+    HT hv[KK];
+    S dg;
+    if constexpr (PF) {
+      const int cidx = pidx;
+      const HT chop = phop;
+      fetch_next(gi + step);
+#pragma unroll
+      for (int k = 0; k < KK; ++k) {
+        idx[k] = __shfl_sync(0xffffffffu, cidx, k, G);
+        hv[k] = shfl_g(chop, k, G);
+      }
+      dg = get_re(shfl_g(chop, KK, G));
+    }
+    if (gi >= ge) continue;
     const int i = (int)(gi >> gs);
-    const int r0 = (int)(gi & gmask) * VPT;
+    const int r0 = lg * VPT;
     const size_t base = (size_t)i * R + r0;
     V own[VPT], acc[VPT], lv[VPT];
-    int idx[KK];
-    typename Ell<FP64, CH>::HT hv[KK];
+    if constexpr (!PF) {
 #pragma unroll
-    for (int k = 0; k < KK; ++k) {
-      const size_t s = (size_t)k * H.n + i;
-      idx[k] = __ldg(H.idx + s);
-      hv[k] = __ldg(H.hop2 + s);
+      for (int k = 0; k < KK; ++k) {
+        const size_t s = (size_t)k * H.n + i;
+        idx[k] = __ldg(H.idx + s);
+        hv[k] = __ldg(H.hop2 + s);
+      }
+      dg = __ldg(H.diag2 + i);
     }
-    const S dg = __ldg(H.diag2 + i);
     ldg_v<VPT>(own, tm1 + base);
     if (first) {
 #pragma unroll
@@ -1310,7 +1374,7 @@ __device__ __forceinline__ void write_partials_vpt(double2 (&v)[NQ * VPT], int R
   }
 }
 
-template <bool FP64, bool CH, int VPT, int KK>
+template <bool FP64, bool CH, int VPT, int KK, bool PF = false>
 __global__ void __launch_bounds__(128, 5) k_cheb_re_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
                                                        const typename Prec<FP64>::V* __restrict__ tm1,
                                                        const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
@@ -1320,9 +1384,9 @@ __global__ void __launch_bounds__(128, 5) k_cheb_re_wv(Ell<FP64, CH> H, const in
   using V = typename Prec<FP64>::V;
   DotAcc<V> d0[VPT], d1[VPT], nl[VPT], nr[VPT];
   if (first)
-    cheb_wave_vpt<FP64, CH, VPT, false, KK, true>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
+    cheb_wave_vpt<FP64, CH, VPT, false, KK, true, PF>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
   else
-    cheb_wave_vpt<FP64, CH, VPT, false, KK, false>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
+    cheb_wave_vpt<FP64, CH, VPT, false, KK, false, PF>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, l, d0, d1, nl, nr);
   const int G = 1 << gs;
   if (first) {
     double2 v[3 * VPT];
@@ -1343,17 +1407,19 @@ __global__ void __launch_bounds__(128, 5) k_cheb_re_wv(Ell<FP64, CH> H, const in
   }
 }
 
-template <bool FP64, bool CH, int VPT, int KK>
-__global__ void __launch_bounds__(128, 6) k_cheb_dbl_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+template <bool FP64, bool CH, int VPT, int KK, bool PF = false>
+__global__ void __launch_bounds__(128, PF ? 5 : 6) k_cheb_dbl_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
                                                         const typename Prec<FP64>::V* __restrict__ tm1,
                                                         const typename Prec<FP64>::V* tm2, typename Prec<FP64>::V* tout,
                                                         double2* __restrict__ partial, int nblocks, int m) {
   using V = typename Prec<FP64>::V;
   DotAcc<V> a0[VPT], a1[VPT], u0[VPT], u1[VPT];
   if (m == 1)
-    cheb_wave_vpt<FP64, CH, VPT, true, KK, true>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
+    cheb_wave_vpt<FP64, CH, VPT, true, KK, true, PF>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0,
+                                                     u1);
   else
-    cheb_wave_vpt<FP64, CH, VPT, true, KK, false>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
+    cheb_wave_vpt<FP64, CH, VPT, true, KK, false, PF>(H, tab[blockIdx.x], R, gs, tm1, tm2, tout, nullptr, a0, a1, u0,
+                                                      u1);
   double2 v[2 * VPT];
 #pragma unroll
   for (int w = 0; w < VPT; ++w) {

@@ -257,3 +257,46 @@ def test_update_hamiltonian_equals_fresh_build():
     with pytest.raises(g.GqtError) as e:
         g.gqt_update_hamiltonian(ham, lat2.onsite, bad)
     assert e.value.status == g.GQT_EINVAL
+
+
+@pytest.mark.parametrize("name,R", [("cubic", 32), ("cubic", 16), ("honeycomb_phases", 8), ("honeycomb_phases", 16),
+                                    ("ragged_cubic", 32), ("ragged_honeycomb", 16)])
+def test_fp32_multivector_prefetch_matches_oracle(name, R):
+    """FP32 multi-vector moment kernels whose lane group per site holds at least K + 1
+    lanes fetch the next site's indices, hoppings and diagonal one iteration ahead and
+    share them by shuffles.  DOS (l = r, two moments per order) and VAC rows equal
+    the oracle's for sampled vectors, including segments whose ends fall inside a
+    warp (odd site counts) and complex hoppings."""
+    if name == "cubic":
+        lat, dE = S.cubic(13, -1.0, 16.5, seed=6), S.energy_scale_rule(6, -1.0, 16.5)
+        parts = [lat]
+    elif name == "honeycomb_phases":
+        lat = S.with_random_bond_phases(S.honeycomb(23, 17, -2.7, 2.0, seed=4), 5)
+        dE, parts = S.energy_scale_rule(3, -2.7, 2.0), [lat]
+    elif name == "ragged_cubic":
+        parts = [S.cubic(L, -1.0, 16.5, seed=40 + q) for q, L in enumerate((5, 7, 3, 6))]
+        lat, dE = S.block_diagonal(parts), S.energy_scale_rule(6, -1.0, 16.5)
+    else:
+        parts = [S.honeycomb(a, b, -2.7, 1.0, seed=50 + q) for q, (a, b) in enumerate(((5, 3), (9, 7), (4, 4)))]
+        lat, dE = S.block_diagonal(parts), S.energy_scale_rule(3, -2.7, 1.0)
+    ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP32_ACC64)
+    assert ham.nseg == len(parts)
+    ph = S.random_phase(lat.n, R, seed=12)
+    if len(parts) > 1:  # unit norm per segment
+        for q, p in enumerate(parts):
+            o = lat.seg_offsets[q]
+            ph[o:o + p.n] *= np.sqrt(lat.n / p.n)
+    d = torch.from_numpy(ph).to(torch.complex64).cuda()
+    M = 97
+    mu = np.empty((len(parts), R, M))
+    g.gqt_dos_moments(ham, d, R, M, mu)
+    dts = np.array([0.5])
+    Np = [O.np_rule(dE * 0.5, 64)]
+    vac = _vac(ham, d, dts, M, Np)
+    for q, p in enumerate(parts):
+        o = 0 if len(parts) == 1 else lat.seg_offsets[q]
+        h = O.Hamiltonian(p, dE)
+        for r in (0, R // 2 - 1, R - 1):
+            seg = ph[o:o + p.n, r]
+            assert nerr(mu[q, r], h.dos_moments(seg, M)) < 2e-5
+            assert nerr(vac[0, q, r], h.vac_moments(seg, dts, Np, M)[0]) < 1e-4
