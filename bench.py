@@ -139,11 +139,20 @@ def bytes_per_orbital_cheb(K: int, fp64: bool, hop_real: bool, R: int) -> float:
     return 4 * v * R + K * (4 + hop) + s
 
 
+def bytes_per_orbital_pair(K: int, hop_real: bool, R: int) -> float:
+    """Algorithmic bytes per orbital per step of the two-recurrence kernel (FP64):
+    per vector element A and B of orders k-1 (gather counted once), k-2 and k
+    (6 complex values); H~ once per site."""
+    return 6 * 16 * R + K * (4 + (8 if hop_real else 16)) + 8
+
+
 def fp64_fma_per_orbital(K: int, hop_real: bool, dot: str) -> int:
-    """Algorithmic FP64 fused multiply-adds per orbital per order: the recurrence
+    """Algorithmic FP64 fused multiply-adds per orbital per launch: the recurrence
     (diagonal 2, each neighbour 2 real or 4 complex) plus the moment dot products
-    (Re <l|T_m>: 2; the l = r kernel's <u|u> and Re <u_m|u_m-1>: 4)."""
-    return 2 + K * (2 if hop_real else 4) + (2 if dot == "re" else 4)
+    (Re <l|T_m>: 2; the l = r kernel's <u|u> and Re <u_m|u_m-1>: 4); the
+    two-recurrence kernel runs two recurrences and two Re dots (4)."""
+    rec = 2 + K * (2 if hop_real else 4)
+    return {"re": rec + 2, "dbl": rec + 4, "pair": 2 * rec + 4}[dot]
 
 
 def fp32_batched(args, g, torch):
@@ -468,7 +477,7 @@ def run_ours(args):
         e1.record(st)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        prof_ms, prof_n = g.gqt_profile_stop(6)
+        prof_ms, prof_n = g.gqt_profile_stop(7)
     launches = g.gqt_launch_count() - launches0
     t_ms = e0.elapsed_time(e1)
     if ws > 1:
@@ -498,30 +507,33 @@ def run_ours(args):
                                     "d2h_bytes_per_step": 4 * vb + 2 * M * 8}
 
     # roofline of the dominant kernel family (largest share of the timed kernel time):
-    # family 1 = VAC orders Re <l|T_m|r> (k_cheb_re), 5 = MSD orders with l = r, two
-    # moments per step (k_cheb_dbl, no l read).
+    # family 1 = VAC orders Re <l|T_m|r> by one recurrence (k_cheb_re), 5 = MSD orders
+    # with l = r, two moments per step (k_cheb_dbl, no l read), 6 = VAC orders by two
+    # recurrences, two moments per step (k_cheb_pair).
     hbm, peak_kind = _peaks()
     fam = {1: ("k_cheb_re (VAC row: fused SpMV + three-term recurrence + Re <l|T_m|r>)",
-               bytes_per_orbital_cheb(3, True, ham.hop_real, R)),
+               bytes_per_orbital_cheb(3, True, ham.hop_real, R), "re"),
            5: ("k_cheb_dbl (MSD row: fused SpMV + recurrence + <u_n|u_n>, <u_n+1|u_n>)",
-               bytes_per_orbital_cheb(3, True, ham.hop_real, R) - 16 * R)}
+               bytes_per_orbital_cheb(3, True, ham.hop_real, R) - 16 * R, "dbl"),
+           6: ("k_cheb_pair (VAC row: two fused SpMV + recurrences, T_k l and T_k r, + Re <A_k|B_k>, Re <A_k|B_k+1>)",
+               bytes_per_orbital_pair(3, ham.hop_real, R), "pair")}
     total_prof = float(np.sum(prof_ms))
     dom = max(fam, key=lambda k: prof_ms[k])
     fams = {}
-    for k, (name, bpo_k) in fam.items():
+    for k, (name, bpo_k, _) in fam.items():
         nl = int(prof_n[k])
         avg = prof_ms[k] * 1e-3 / max(nl, 1)
         fams[name.split()[0]] = {"launches": nl, "avg_launch_us": avg * 1e6, "bytes_per_orbital": bpo_k,
                                  "achieved_gbs": N * bpo_k / avg / 1e9 if nl else None,
                                  "share_of_timed_kernels": prof_ms[k] / max(total_prof, 1e-12)}
-    kname, bpo = fam[dom]
-    traffic = measured_traffic("k_cheb_re" if dom == 1 else "k_cheb_dbl", N)
+    kname, bpo, fkind = fam[dom]
+    traffic = measured_traffic(kname.split()[0], N)
     n_launch = int(prof_n[dom])
     avg_s = prof_ms[dom] * 1e-3 / max(n_launch, 1)
     achieved = N * bpo / avg_s / 1e9
     # FP64 arithmetic roofline of the same kernel against the measured FMA peak
     fp64_peak = g.gqt_probe_fp64()
-    fma = fp64_fma_per_orbital(3, ham.hop_real, "re" if dom == 1 else "dbl") * R
+    fma = fp64_fma_per_orbital(3, ham.hop_real, fkind) * R
     fp64_achieved = 2.0 * fma * N / avg_s / 1e9
     hbm_frac, alu_frac = achieved / hbm, fp64_achieved / fp64_peak
     out = {

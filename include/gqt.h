@@ -267,6 +267,15 @@ gqt_status gqt_autotune(gqt_ham* ham, int R, int* threads, int* blocks_per_sm, i
  * one-launch-per-order path. */
 gqt_status gqt_set_cluster(gqt_ham* ham, int enable);
 
+/* Moment rows Re <l|T_m|r> with l != r (VAC rows, gqt_vac_moments) by two
+ * recurrences at once (default 1): A_k = T_k l and B_k = T_k r give
+ * mu_2k = 2 Re <A_k|B_k> - mu_0 and mu_2k+1 = 2 Re <A_k|B_k+1> - mu_1
+ * (Chebyshev product identities, H~ Hermitian), so each step streams H~ once for
+ * two moments.  Applies to the wavefront kernels (not the multi-vector FP32
+ * form, the chunk-ordered variant 0 or cluster rows).  0 runs one recurrence on
+ * r with a dot against l per order. */
+gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
+
 /* Use CUDA graphs for repeated loops (default 1). */
 gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
 
@@ -276,7 +285,8 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
  * milliseconds and the launch count: 0 = first moment order, 1 = moment orders
  * m >= 2 with l != r (the fused SpMV + recurrence + dot kernel), 2 = one-set
  * evolution order, 3 = two-set evolution order, 4 = coupled commutator order,
- * 5 = moment steps m >= 2 with l = r (two moments per step).  Graph
+ * 5 = moment steps m >= 2 with l = r (two moments per step), 6 = moment steps
+ * m >= 2 of the two-recurrence l != r rows (two moments per step).  Graph
  * capture is bypassed while profiling. */
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);

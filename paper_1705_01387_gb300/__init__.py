@@ -68,6 +68,7 @@ _SIGS = {
     "gqt_set_graphs": [_P, _I],
     "gqt_set_variant": [_P, _I],
     "gqt_set_cluster": [_P, _I],
+    "gqt_set_vac_pair": [_P, _I],
     "gqt_launch_count": [],
     "gqt_profile_start": [],
     "gqt_probe_fp64": [_P, _P],
@@ -382,6 +383,10 @@ def gqt_set_launch(ham: Ham, threads: int = 0, blocks_per_sm: int = 0):
 
 def gqt_set_cluster(ham: Ham, enable: bool):
     _check(lib().gqt_set_cluster(ham.ptr, int(bool(enable))))
+
+
+def gqt_set_vac_pair(ham: Ham, enable: bool):
+    _check(lib().gqt_set_vac_pair(ham.ptr, int(bool(enable))))
 
 
 def gqt_set_variant(ham: Ham, variant: int):

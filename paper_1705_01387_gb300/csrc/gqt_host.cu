@@ -327,6 +327,36 @@ static int wave_occupancy_k(int R, int variant, int threads, bool dbl) {
   return std::max(1, n);
 }
 
+template <bool FP64, bool CH, int KK>
+static int pair_occupancy_k(int R, int threads) {
+  int n = 0;
+  const size_t smem = (size_t)3 * (threads / 32) * R * sizeof(double2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k_cheb_pair_w<FP64, CH, KK>, threads, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 3;
+  }
+  return std::max(1, n);
+}
+
+template <bool FP64, bool CH>
+static int pair_occupancy(int K, int R, int threads) {
+  switch (K) {
+    case 2: return pair_occupancy_k<FP64, CH, 2>(R, threads);
+    case 3: return pair_occupancy_k<FP64, CH, 3>(R, threads);
+    case 4: return pair_occupancy_k<FP64, CH, 4>(R, threads);
+    default: return pair_occupancy_k<FP64, CH, 6>(R, threads);
+  }
+}
+
+// l != r moment rows by two recurrences: the wavefront kernels' neighbour counts,
+// not the multi-vector (VPT) form.
+static bool pair_applies(const gqt_ham* h, int R) {
+  if (!h->use_pair || h->variant == 0 || h->threads > 256) return false;
+  if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return false;
+  return !((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128);
+}
+
 template <bool FP64, bool CH>
 static int wave_occupancy(int K, int R, int variant, int threads, bool dbl) {
   switch (K) {
@@ -346,7 +376,12 @@ static int moment_grid_per_sm(const gqt_ham* h, int R, int kind) {
   if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return 0;
   const bool dbl = kind == 2;
   int occ;
-  if (h->prec == GQT_FP64)
+  if (kind == 1 && pair_applies(h, R))
+    occ = h->prec == GQT_FP64 ? (h->hop_real ? pair_occupancy<true, false>(h->K, R, h->threads)
+                                             : pair_occupancy<true, true>(h->K, R, h->threads))
+                              : (h->hop_real ? pair_occupancy<false, false>(h->K, R, h->threads)
+                                             : pair_occupancy<false, true>(h->K, R, h->threads));
+  else if (h->prec == GQT_FP64)
     occ = h->hop_real ? wave_occupancy<true, false>(h->K, R, h->variant, h->threads, dbl)
                       : wave_occupancy<true, true>(h->K, R, h->variant, h->threads, dbl);
   else
@@ -588,6 +623,25 @@ static bool launch_cluster_row(gqt_ham* h, const Ell<FP64, CH>& H, const V* r, c
   return false;
 }
 
+template <bool FP64, bool CH, class V>
+static void launch_wave_pair(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTable& T, int R, int rs, const V* am1,
+                             const V* bm1, const V* am2, const V* bm2, V* aout, V* bout, double2* partial, int m,
+                             int slot_norm, cudaStream_t st) {
+  const int4* tab = (const int4*)T.d_tab4.p;
+  const size_t sm = smem_bytes(h, R, 3);
+#define GQT_PAIR(KK)                                                                                              \
+  k_cheb_pair_w<FP64, CH, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, am1, bm1, am2, bm2, aout, bout,  \
+                                                                 partial, T.nblocks, m, slot_norm);              \
+  break;
+  switch (H.K) {
+    case 2: GQT_PAIR(2)
+    case 3: GQT_PAIR(3)
+    case 4: GQT_PAIR(4)
+    default: GQT_PAIR(6)
+  }
+#undef GQT_PAIR
+}
+
 // Launch the moment recursion of r against l and reduce into out, layout
 // [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
 // (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
@@ -634,9 +688,12 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       return;
     }
   }
-  const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p},
+  const bool pair = kind == 1 && pair_applies(h, R);
+  void* wa1 = pair ? h->ws(WS_PA1, vb).p : nullptr;
+  void* wa2 = pair ? h->ws(WS_PA2, vb).p : nullptr;
+  const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p, wa1, wa2},
                                  {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb,
-                                  (double)h->variant});
+                                  (double)h->variant, (double)pair});
   run_graph(h, key, st, [&](cudaStream_t s2) {
     dispatch(h, [&](auto H) {
       using Tr = EllTraits<decltype(H)>;
@@ -646,6 +703,27 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       V* W1 = (V*)w1;
       V* W2 = (V*)w2;
       const int* blk = (const int*)T.d_blk.p;
+      if (pair) {
+        // chain A from l in wa1/wa2, chain B from r in W1/W2; step m yields the dots of
+        // moments 2m-2 and 2m-1, and step 1 the norms (slot 2 * steps)
+        const int steps = (M + 1) / 2;
+        V* A1 = (V*)wa1;
+        V* A2 = (V*)wa2;
+        for (int m = 1; m <= steps; ++m) {
+          const V* am1 = (m == 1) ? lv : ((m - 1) % 2 == 1 ? A1 : A2);
+          const V* bm1 = (m == 1) ? rv : ((m - 1) % 2 == 1 ? W1 : W2);
+          V* aout = (m % 2 == 1) ? A1 : A2;
+          V* bout = (m % 2 == 1) ? W1 : W2;
+          const V* am2 = (m == 1) ? nullptr : ((m == 2) ? lv : aout);
+          const V* bm2 = (m == 1) ? nullptr : ((m == 2) ? rv : bout);
+          size_t pe = prof_begin(s2);
+          launch_wave_pair<Tr::fp64, Tr::ch>(h, H, T, R, rs, am1, bm1, am2, bm2, aout, bout, partial, m, 2 * steps,
+                                             s2);
+          check_launch("k_cheb_pair");
+          prof_end(pe, m == 1 ? 0 : 6, s2);
+        }
+        return;
+      }
       if (kind == 2) {
         const int steps = (M + 1) / 2;  // step m yields moments 2m-2 and 2m-1
         for (int m = 1; m <= std::max(steps, 1); ++m) {
@@ -685,9 +763,9 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
         prof_end(pe, 1, s2);
       }
     });
-    if (kind == 2) {
+    if (kind == 2 || pair) {
       k_reduce_dbl<<<rb, 256, 0, s2>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, 1.0 + tol, (double*)out,
-                                       (int*)h->d_flag.p);
+                                       (int*)h->d_flag.p, pair ? 2 * ((M + 1) / 2) : -1);
       check_launch("k_reduce_dbl");
     } else {
       k_reduce<<<rb, 256, 0, s2>>>(partial, M, nb, R, (const int*)T.d_seg_blk.p, h->nseg, slot_norm,
@@ -973,6 +1051,13 @@ gqt_status gqt_set_cluster(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_cluster = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_vac_pair(gqt_ham* h, int enable) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  h->use_pair = enable != 0;
   API_END
 }
 

@@ -56,6 +56,8 @@ enum WorkSlot {
   WS_ACC0,      // +0, +1
   WS_E1 = 12,   // +0..+3 evolution Chebyshev buffers
   WS_CLUSTER_SEG = 17,
+  WS_PA1 = 18,  // chain A buffers of the two-recurrence (pair) moment rows
+  WS_PA2 = 19,
   WS_ADJ0 = 20  // adjoint workspace slots start here
 };
 
@@ -84,6 +86,7 @@ struct gqt_ham {
   int variant = 2;  // moment kernels: 0 chunk order, 1 wavefront, 2 wavefront with two elements per thread
   bool use_graphs = true;
   bool use_cluster = true;  // cluster-resident moment rows for small systems
+  bool use_pair = true;     // l != r moment rows by two recurrences (two moments per step)
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

@@ -610,23 +610,31 @@ __global__ void k_cheb_dbl(Ell<FP64, CH> H, const int* __restrict__ blk, int R, 
 // each s summed over the segment's CTAs in CTA order.  Bound |mu_k| <= (1+tol) mu_0.
 static __global__ void k_reduce_dbl(const double2* __restrict__ partial, int M, int nblocks, int R,
                              const int* __restrict__ seg_blk, int nseg, double bound_factor, double* __restrict__ out,
-                             int* __restrict__ flag) {
+                             int* __restrict__ flag, int slot_norm = -1) {
+  // slot_norm < 0: l = r, |mu_k| <= mu_0 (1 + tol); otherwise slot_norm holds
+  // (|l|^2, |r|^2) and |mu_k| <= |l| |r| (1 + tol).
   const size_t total = (size_t)nseg * R * M;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % R);
     const int k = (int)((t / R) % M);
     const int s = (int)(t / ((size_t)R * M));
-    double sk = 0.0, s0 = 0.0, sp = 0.0;
+    double sk = 0.0, s0 = 0.0, sp = 0.0, nl = 0.0, nr = 0.0;
     const int kp = k & 1;
     for (int b = seg_blk[s]; b < seg_blk[s + 1]; ++b) {
       sk += partial[((size_t)k * nblocks + b) * R + r].x;
       s0 += partial[((size_t)0 * nblocks + b) * R + r].x;
       sp += partial[((size_t)kp * nblocks + b) * R + r].x;
+      if (slot_norm >= 0) {
+        const double2 q = partial[((size_t)slot_norm * nblocks + b) * R + r];
+        nl += q.x;
+        nr += q.y;
+      }
     }
     const double mu = (k < 2) ? sk : 2.0 * sk - sp;
     out[((size_t)s * R + r) * M + k] = mu;
     if (!isfinite(mu)) atomicOr(flag, 4);
-    if (fabs(mu) > s0 * bound_factor + 1e-300) atomicOr(flag, 2);
+    const double bound = (slot_norm >= 0 ? sqrt(nl * nr) : s0) * bound_factor + 1e-300;
+    if (fabs(mu) > bound) atomicOr(flag, 2);
   }
 }
 
@@ -1157,6 +1165,113 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_dbl_w(Ell<FP64, 
   }
 }
 
+
+// Re <l|T_m(H~)|r> for l != r by two recurrences at once (Eqs. 21, 29): chain A
+// from l and chain B from r, A_k = T_k l, B_k = T_k r.  The product identities
+// T_2k = 2 T_k T_k - T_0 and T_2k+1 = 2 T_k T_k+1 - T_1 of Chebyshev polynomials,
+// with T_k(H~) Hermitian, give mu_2k = 2 Re <A_k|B_k> - mu_0 and mu_2k+1 =
+// 2 Re <A_k|B_k+1> - mu_1, so step m (computing A_m, B_m) yields the dots of
+// moments 2m-2 (<A_m-1|B_m-1>) and 2m-1 (<A_m-1|B_m>), combined in k_reduce_dbl.
+// Each step streams H~ once for two moments; FP64 work per moment is the same as
+// the single recurrence with its Re <l|.> dot.  Step 1 also records |l|^2, |r|^2
+// (slot_norm) for the moment bound.  Wavefront order, one element per thread.
+template <bool FP64, bool CH, int KK, bool first>
+__device__ __forceinline__ void cheb_pair_body(const Ell<FP64, CH>& H, int4 tb, int R, int rs,
+                                               const typename Prec<FP64>::V* __restrict__ am1,
+                                               const typename Prec<FP64>::V* __restrict__ bm1,
+                                               const typename Prec<FP64>::V* am2, const typename Prec<FP64>::V* bm2,
+                                               typename Prec<FP64>::V* aout, typename Prec<FP64>::V* bout,
+                                               DotAcc<typename Prec<FP64>::V>& d0, DotAcc<typename Prec<FP64>::V>& d1,
+                                               DotAcc<typename Prec<FP64>::V>& nl, DotAcc<typename Prec<FP64>::V>& nr) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  using HT = typename Ell<FP64, CH>::HT;
+  const size_t segb = (size_t)tb.x << rs, sege = (size_t)tb.y << rs;
+  const size_t step = (size_t)tb.w * blockDim.x;
+  const int r = threadIdx.x & (R - 1);
+  for (size_t e = segb + (size_t)tb.z * blockDim.x + threadIdx.x; e < sege; e += step) {
+    const int i = (int)(e >> rs);
+    int idx[KK];
+    HT hv[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      const size_t s = (size_t)k * H.n + i;
+      idx[k] = __ldg(H.idx + s);
+      hv[k] = __ldg(H.hop2 + s);
+    }
+    const S dg = __ldg(H.diag2 + i);
+    const V ao = __ldg(am1 + e), bo = __ldg(bm1 + e);
+    V a, b;
+    if (first) {
+      a = cscale(ao, dg);
+      b = cscale(bo, dg);
+    } else {
+      a = cmul_acc(cneg(am2[e]), dg, ao);
+      b = cmul_acc(cneg(bm2[e]), dg, bo);
+    }
+    V na[KK], nb[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      const size_t j = ((size_t)idx[k] << rs) + r;
+      na[k] = __ldg(am1 + j);
+      nb[k] = __ldg(bm1 + j);
+    }
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      a = cmul_acc(a, hv[k], na[k]);
+      b = cmul_acc(b, hv[k], nb[k]);
+    }
+    if (first) {
+      a = cscale(a, (S)0.5);
+      b = cscale(b, (S)0.5);
+    }
+    aout[e] = a;
+    bout[e] = b;
+    d0.add_re(ao, bo);
+    d1.add_re(ao, b);
+    if (first) {
+      nl.add_norm(ao);
+      nr.add_norm(bo);
+    }
+  }
+}
+
+template <bool FP64, bool CH, int KK>
+__global__ void __launch_bounds__(256, 3) k_cheb_pair_w(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int rs,
+                                                       const typename Prec<FP64>::V* __restrict__ am1,
+                                                       const typename Prec<FP64>::V* __restrict__ bm1,
+                                                       const typename Prec<FP64>::V* am2,
+                                                       const typename Prec<FP64>::V* bm2,
+                                                       typename Prec<FP64>::V* aout, typename Prec<FP64>::V* bout,
+                                                       double2* __restrict__ partial, int nblocks, int m,
+                                                       int slot_norm) {
+  using V = typename Prec<FP64>::V;
+  double2* smem = dyn_smem();
+  const int b = blockIdx.x;
+  DotAcc<V> d0, d1, nl, nr;
+  if (m == 1)
+    cheb_pair_body<FP64, CH, KK, true>(H, tab[b], R, rs, am1, bm1, am2, bm2, aout, bout, d0, d1, nl, nr);
+  else
+    cheb_pair_body<FP64, CH, KK, false>(H, tab[b], R, rs, am1, bm1, am2, bm2, aout, bout, d0, d1, nl, nr);
+  const int k0 = 2 * m - 2;
+  if (m == 1) {
+    double2 v[3] = {d0.get(), d1.get(), make_double2(nl.get().x, nr.get().x)};
+    block_reduce_r<3>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+      partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
+    }
+  } else {
+    double2 v[2] = {d0.get(), d1.get()};
+    block_reduce_r<2>(v, R, smem);
+    if ((int)threadIdx.x < R) {
+      partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
+      partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+    }
+  }
+}
+
 }  // namespace gqt
 
 namespace gqt {
@@ -1185,43 +1300,58 @@ namespace gqt {
 // site's H~ row (indices, hoppings, diagonal) is loaded once for VPT vectors
 // and every vector access is a VPT-wide contiguous load (16-byte loads for
 // FP32 pairs), so instruction count per vector element drops by ~VPT.
+// Vector tiles of the multi-vector kernels.  Lane lg of a site's G-lane group holds
+// VPT of the site's R = G * VPT vectors, interleaved so that each load instruction
+// of the group covers whole contiguous runs: FP32 pairs (16 B) at element offsets
+// 2 lg + q G (q = 0, 2, ..), FP64 vectors (16 B) at lg + q G.  d[q] is vector
+// vec_of<FP64>(lg, q, G) of the site.  ldg_v reads T_m (own and neighbour tiles,
+// reused from L2 by later sites); ld_v and st_v move the read-once streams
+// (T_{m-1}, the left vector, T_{m+1}) with the streaming (evict-first) hint so that
+// they do not push T_m's reuse window out of L2.
+template <bool FP64>
+__device__ __forceinline__ int lane_offset(int lg) { return FP64 ? lg : 2 * lg; }
+template <bool FP64>
+__device__ __forceinline__ int vec_of(int lg, int q, int G) {
+  return FP64 ? q * G + lg : (q & ~1) * G + 2 * lg + (q & 1);
+}
 template <int VPT>
-__device__ __forceinline__ void ldg_v(float2 (&d)[VPT], const float2* __restrict__ p) {
+__device__ __forceinline__ void ldg_v(float2 (&d)[VPT], const float2* __restrict__ p, int G) {
 #pragma unroll
   for (int q = 0; q < VPT; q += 2) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p + q));
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p + (size_t)q * G));
     d[q] = make_float2(t.x, t.y);
     d[q + 1] = make_float2(t.z, t.w);
   }
 }
 template <int VPT>
-__device__ __forceinline__ void ld_v(float2 (&d)[VPT], const float2* p) {
+__device__ __forceinline__ void ld_v(float2 (&d)[VPT], const float2* p, int G) {
 #pragma unroll
   for (int q = 0; q < VPT; q += 2) {
-    const float4 t = *reinterpret_cast<const float4*>(p + q);
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p + (size_t)q * G));
     d[q] = make_float2(t.x, t.y);
     d[q + 1] = make_float2(t.z, t.w);
   }
 }
 template <int VPT>
-__device__ __forceinline__ void st_v(float2* p, const float2 (&d)[VPT]) {
+__device__ __forceinline__ void st_v(float2* p, const float2 (&d)[VPT], int G) {
 #pragma unroll
-  for (int q = 0; q < VPT; q += 2) *reinterpret_cast<float4*>(p + q) = make_float4(d[q].x, d[q].y, d[q + 1].x, d[q + 1].y);
+  for (int q = 0; q < VPT; q += 2)
+    __stcs(reinterpret_cast<float4*>(p + (size_t)q * G), make_float4(d[q].x, d[q].y, d[q + 1].x, d[q + 1].y));
 }
 template <int VPT>
-__device__ __forceinline__ void ldg_v(double2 (&d)[VPT], const double2* __restrict__ p) {
+__device__ __forceinline__ void ldg_v(double2 (&d)[VPT], const double2* __restrict__ p, int G) {
 #pragma unroll
-  for (int q = 0; q < VPT; ++q) d[q] = __ldg(p + q);
+  for (int q = 0; q < VPT; ++q) d[q] = __ldg(p + (size_t)q * G);
 }
 template <int VPT>
-__device__ __forceinline__ void ld_v(double2 (&d)[VPT], const double2* p) {
+__device__ __forceinline__ void ld_v(double2 (&d)[VPT], const double2* p, int G) {
 #pragma unroll
-  for (int q = 0; q < VPT; ++q) d[q] = p[q];
+  for (int q = 0; q < VPT; ++q) d[q] = __ldcs(p + (size_t)q * G);
 }
 template <int VPT>
-__device__ __forceinline__ void st_v(double2* p, const double2 (&d)[VPT]) {
+__device__ __forceinline__ void st_v(double2* p, const double2 (&d)[VPT], int G) {
 #pragma unroll
-  for (int q = 0; q < VPT; ++q) p[q] = d[q];
+  for (int q = 0; q < VPT; ++q) __stcs(p + (size_t)q * G, d[q]);
 }
 
 // One recurrence order for VPT vectors of each site, wavefront order over groups
@@ -1306,7 +1436,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
     }
     if (gi >= ge) continue;
     const int i = (int)(gi >> gs);
-    const int r0 = lg * VPT;
+    const int r0 = lane_offset<FP64>(lg);
     const size_t base = (size_t)i * R + r0;
     V own[VPT], acc[VPT], lv[VPT];
     if constexpr (!PF) {
@@ -1318,7 +1448,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
       }
       dg = __ldg(H.diag2 + i);
     }
-    ldg_v<VPT>(own, tm1 + base);
+    ldg_v<VPT>(own, tm1 + base, G);
     if (first) {
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
@@ -1326,15 +1456,15 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
         acc[v].y = 0;
       }
     } else {
-      ld_v<VPT>(acc, tm2 + base);
+      ld_v<VPT>(acc, tm2 + base, G);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) acc[v] = cneg(acc[v]);
     }
-    if (!DBL) ldg_v<VPT>(lv, l + base);
+    if (!DBL) ld_v<VPT>(lv, l + base, G);
 #pragma unroll
     for (int k = 0; k < KK; ++k) {
       V nb[VPT];
-      ldg_v<VPT>(nb, tm1 + (size_t)idx[k] * R + r0);
+      ldg_v<VPT>(nb, tm1 + (size_t)idx[k] * R + r0, G);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) acc[v] = cmul_acc(acc[v], hv[k], nb[v]);
     }
@@ -1343,7 +1473,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
       acc[v] = cmul_acc(acc[v], dg, own[v]);
       if (first) acc[v] = cscale(acc[v], (S)0.5);
     }
-    st_v<VPT>(tout + base, acc);
+    st_v<VPT>(tout + base, acc, G);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       if (DBL) {
@@ -1361,7 +1491,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
   }
 }
 
-template <int VPT, int NQ>
+template <bool FP64, int VPT, int NQ>
 __device__ __forceinline__ void write_partials_vpt(double2 (&v)[NQ * VPT], int R, int G, double2* smem,
                                                    double2* __restrict__ partial, int nblocks, const int (&slot)[NQ]) {
   block_reduce_r<NQ * VPT>(v, G, smem);
@@ -1370,7 +1500,7 @@ __device__ __forceinline__ void write_partials_vpt(double2 (&v)[NQ * VPT], int R
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
       for (int w = 0; w < VPT; ++w)
-        partial[((size_t)slot[q] * nblocks + blockIdx.x) * R + threadIdx.x * VPT + w] = v[q * VPT + w];
+        partial[((size_t)slot[q] * nblocks + blockIdx.x) * R + vec_of<FP64>(threadIdx.x, w, G)] = v[q * VPT + w];
   }
 }
 
@@ -1397,13 +1527,13 @@ __global__ void __launch_bounds__(128, 5) k_cheb_re_wv(Ell<FP64, CH> H, const in
       v[2 * VPT + w] = make_double2(nl[w].get().x, nr[w].get().x);
     }
     const int slots[3] = {slot0, slot0 + 1, slot_norm};
-    write_partials_vpt<VPT, 3>(v, R, G, dyn_smem(), partial, nblocks, slots);
+    write_partials_vpt<FP64, VPT, 3>(v, R, G, dyn_smem(), partial, nblocks, slots);
   } else {
     double2 v[VPT];
 #pragma unroll
     for (int w = 0; w < VPT; ++w) v[w] = d1[w].get();
     const int slots[1] = {slot0};
-    write_partials_vpt<VPT, 1>(v, R, G, dyn_smem(), partial, nblocks, slots);
+    write_partials_vpt<FP64, VPT, 1>(v, R, G, dyn_smem(), partial, nblocks, slots);
   }
 }
 
@@ -1427,7 +1557,7 @@ __global__ void __launch_bounds__(128, PF ? 5 : 6) k_cheb_dbl_wv(Ell<FP64, CH> H
     v[VPT + w] = a1[w].get();
   }
   const int slots[2] = {2 * m - 2, 2 * m - 1};
-  write_partials_vpt<VPT, 2>(v, R, 1 << gs, dyn_smem(), partial, nblocks, slots);
+  write_partials_vpt<FP64, VPT, 2>(v, R, 1 << gs, dyn_smem(), partial, nblocks, slots);
 }
 
 }  // namespace gqt

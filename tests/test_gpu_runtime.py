@@ -300,3 +300,90 @@ def test_fp32_multivector_prefetch_matches_oracle(name, R):
             seg = ph[o:o + p.n, r]
             assert nerr(mu[q, r], h.dos_moments(seg, M)) < 2e-5
             assert nerr(vac[0, q, r], h.vac_moments(seg, dts, Np, M)[0]) < 1e-4
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("name,R", [("cubic", 4), ("cubic", 32), ("honeycomb_phases", 8), ("ragged_honeycomb", 16)])
+def test_fp64_multivector_tiles_match_oracle(name, R, variant):
+    """FP64 storage with 128-thread CTAs runs the multi-vector kernels (two or four
+    vectors per lane, interleaved across the site's lane group): DOS and VAC rows
+    equal the oracle's to FP64 accuracy for every sampled vector."""
+    if name == "cubic":
+        parts = [S.cubic(11, -1.0, 16.5, seed=7)]
+        dE = S.energy_scale_rule(6, -1.0, 16.5)
+    elif name == "honeycomb_phases":
+        parts = [S.with_random_bond_phases(S.honeycomb(19, 13, -2.7, 2.0, seed=8), 6)]
+        dE = S.energy_scale_rule(3, -2.7, 2.0)
+    else:
+        parts = [S.honeycomb(a, b, -2.7, 1.0, seed=60 + q) for q, (a, b) in enumerate(((7, 3), (5, 9), (4, 4)))]
+        dE = S.energy_scale_rule(3, -2.7, 1.0)
+    lat = parts[0] if len(parts) == 1 else S.block_diagonal(parts)
+    ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP64)
+    g.gqt_set_launch(ham, 128, 0)
+    g.gqt_set_variant(ham, variant)
+    ph = S.random_phase(lat.n, R, seed=13)
+    if len(parts) > 1:
+        for q, p in enumerate(parts):
+            o = lat.seg_offsets[q]
+            ph[o:o + p.n] *= np.sqrt(lat.n / p.n)
+    d = torch.from_numpy(ph).cuda()
+    M = 89
+    mu = np.empty((len(parts), R, M))
+    g.gqt_dos_moments(ham, d, R, M, mu)
+    dts = np.array([0.4])
+    Np = [O.np_rule(dE * 0.4, 64)]
+    vac = _vac(ham, d, dts, M, Np)
+    for q, p in enumerate(parts):
+        o = 0 if len(parts) == 1 else lat.seg_offsets[q]
+        h = O.Hamiltonian(p, dE)
+        for r in sorted({0, 1, R // 2, R - 1}):
+            seg = ph[o:o + p.n, r]
+            assert nerr(mu[q, r], h.dos_moments(seg, M)) < 1e-10
+            assert nerr(vac[0, q, r], h.vac_moments(seg, dts, Np, M)[0]) < 1e-10
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 96, 97])
+@pytest.mark.parametrize("name,R", [("honeycomb", 1), ("square_phases", 2), ("chain", 1), ("ragged_honeycomb", 1),
+                                    ("cubic_fp32", 1)])
+def test_vac_pair_rows_match_oracle(name, R, M):
+    """VAC rows by two recurrences (A_k = T_k l, B_k = T_k r; mu_2k = 2 Re <A_k|B_k> -
+    mu_0, mu_2k+1 = 2 Re <A_k|B_k+1> - mu_1) equal the oracle's single-recurrence
+    moments and the library's own one-recurrence path, for odd and even M."""
+    prec = g.GQT_FP64
+    if name == "honeycomb":
+        parts, dE = [S.honeycomb(29, 21, -2.7, 1.0, seed=3)], S.energy_scale_rule(3, -2.7, 1.0)
+    elif name == "square_phases":
+        parts, dE = [S.with_random_bond_phases(S.square(27, 23, -1.0, 2.0, seed=4), 9)], 5.2
+    elif name == "chain":
+        parts, dE = [S.chain(2999, -1.0, 4.0, seed=2)], 4.2
+    elif name == "ragged_honeycomb":
+        parts = [S.honeycomb(a, b, -2.7, 1.0, seed=70 + q) for q, (a, b) in enumerate(((7, 3), (11, 9), (4, 4)))]
+        dE = S.energy_scale_rule(3, -2.7, 1.0)
+    else:
+        parts, dE, prec = [S.cubic(13, -1.0, 16.5, seed=6)], S.energy_scale_rule(6, -1.0, 16.5), g.GQT_FP32_ACC64
+    lat = parts[0] if len(parts) == 1 else S.block_diagonal(parts)
+    ham = g.gqt_build_hamiltonian(lat, dE, prec)
+    g.gqt_set_cluster(ham, False)
+    ph = S.random_phase(lat.n, R, seed=14)
+    if len(parts) > 1:
+        for q, p in enumerate(parts):
+            o = lat.seg_offsets[q]
+            ph[o:o + p.n] *= np.sqrt(lat.n / p.n)
+    d = torch.from_numpy(ph).to(torch.complex128 if prec == g.GQT_FP64 else torch.complex64).cuda()
+    dts = np.array([0.45, 0.3])
+    Np = [O.np_rule(dE * x, 64) for x in dts]
+    got = {}
+    for pair in (True, False):
+        g.gqt_set_vac_pair(ham, pair)
+        got[pair] = _vac(ham, d, dts, M, Np)
+    tol = 1e-10 if prec == g.GQT_FP64 else 1e-4
+    for q, p in enumerate(parts):
+        o = 0 if len(parts) == 1 else lat.seg_offsets[q]
+        h = O.Hamiltonian(p, dE)
+        for r in range(R):
+            ref = h.vac_moments(ph[o:o + p.n, r], dts, Np, M)
+            for k in range(len(dts)):
+                assert nerr(got[True][k, q, r], ref[k]) < tol
+                assert nerr(got[False][k, q, r], ref[k]) < tol
+    if prec == g.GQT_FP64:
+        assert nerr(got[True], got[False]) < 1e-12
