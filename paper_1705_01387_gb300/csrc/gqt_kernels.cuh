@@ -228,6 +228,29 @@ __device__ __forceinline__ void block_reduce_r(double2 (&v)[NV], int R, double2*
   }
 }
 
+// block_reduce_r for real values (Re dots and norms have no imaginary part): half
+// the FP64 adds, which matters where the FP64 pipe bounds the kernel.
+template <int NV>
+__device__ __forceinline__ void block_reduce_rx(double (&v)[NV], int R, double* smem /*[NV][warps][R]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int off = 16; off >= R; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+  if (lane < R) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) smem[(q * nw + warp) * R + lane] = v[q];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < R) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += smem[(q * nw + w) * R + threadIdx.x];
+      v[q] = t;
+    }
+  }
+}
+
 // y = sum_k hop2[k][i] * x[idx[k][i]*R + r] + diag2[i] * x[i*R + r]  (= 2 H~ x, element (i, r)).
 template <bool FP64, bool CH>
 __device__ __forceinline__ typename Prec<FP64>::V apply2h(const Ell<FP64, CH>& H, const typename Prec<FP64>::V* __restrict__ x,
@@ -597,12 +620,12 @@ __global__ void k_cheb_dbl(Ell<FP64, CH> H, const int* __restrict__ blk, int R, 
     a0.add_norm(own);
     a1.add_re(acc, own);
   }
-  double2 v[2] = {a0.get(), a1.get()};
-  block_reduce_r<2>(v, R, smem);
+  double v[2] = {a0.get().x, a1.get().x};
+  block_reduce_rx<2>(v, R, (double*)smem);
   if ((int)threadIdx.x < R) {
     const int k0 = 2 * m - 2;
-    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
-    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = make_double2(v[0], 0.0);
+    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = make_double2(v[1], 0.0);
   }
 }
 
@@ -1136,9 +1159,9 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_re_w(Ell<FP64, C
       partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
     }
   } else {
-    double2 v[1] = {d1.get()};
-    block_reduce_r<1>(v, R, smem);
-    if ((int)threadIdx.x < R) partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = v[0];
+    double v[1] = {d1.get().x};
+    block_reduce_rx<1>(v, R, (double*)smem);
+    if ((int)threadIdx.x < R) partial[((size_t)slot0 * nblocks + b) * R + threadIdx.x] = make_double2(v[0], 0.0);
   }
 }
 
@@ -1156,12 +1179,12 @@ __global__ void __launch_bounds__(256, (U == 1 ? 4 : 2)) k_cheb_dbl_w(Ell<FP64, 
     cheb_wave_body<FP64, CH, U, true, KK, true>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
   else
     cheb_wave_body<FP64, CH, U, true, KK, false>(H, tab[b], R, rs, tm1, tm2, tout, nullptr, a0, a1, u0, u1);
-  double2 v[2] = {a0.get(), a1.get()};
-  block_reduce_r<2>(v, R, smem);
+  double v[2] = {a0.get().x, a1.get().x};
+  block_reduce_rx<2>(v, R, (double*)smem);
   if ((int)threadIdx.x < R) {
     const int k0 = 2 * m - 2;
-    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
-    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+    partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = make_double2(v[0], 0.0);
+    partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = make_double2(v[1], 0.0);
   }
 }
 
@@ -1263,11 +1286,11 @@ __global__ void __launch_bounds__(256, 3) k_cheb_pair_w(Ell<FP64, CH> H, const i
       partial[((size_t)slot_norm * nblocks + b) * R + threadIdx.x] = v[2];
     }
   } else {
-    double2 v[2] = {d0.get(), d1.get()};
-    block_reduce_r<2>(v, R, smem);
+    double v[2] = {d0.get().x, d1.get().x};
+    block_reduce_rx<2>(v, R, (double*)smem);
     if ((int)threadIdx.x < R) {
-      partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = v[0];
-      partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = v[1];
+      partial[((size_t)k0 * nblocks + b) * R + threadIdx.x] = make_double2(v[0], 0.0);
+      partial[((size_t)(k0 + 1) * nblocks + b) * R + threadIdx.x] = make_double2(v[1], 0.0);
     }
   }
 }
