@@ -271,9 +271,9 @@ gqt_status gqt_set_cluster(gqt_ham* ham, int enable);
  * recurrences at once (default 1): A_k = T_k l and B_k = T_k r give
  * mu_2k = 2 Re <A_k|B_k> - mu_0 and mu_2k+1 = 2 Re <A_k|B_k+1> - mu_1
  * (Chebyshev product identities, H~ Hermitian), so each step streams H~ once for
- * two moments.  Applies to the wavefront kernels (not the multi-vector FP32
- * form, the chunk-ordered variant 0 or cluster rows).  0 runs one recurrence on
- * r with a dot against l per order. */
+ * two moments.  Applies to the wavefront kernels, one element per thread or
+ * the multi-vector form (not the chunk-ordered variant 0 or cluster rows).  0
+ * runs one recurrence on r with a dot against l per order. */
 gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
 
 /* Use CUDA graphs for repeated loops (default 1). */

@@ -350,11 +350,37 @@ static int pair_occupancy(int K, int R, int threads) {
 }
 
 // l != r moment rows by two recurrences: the wavefront kernels' neighbour counts,
-// not the multi-vector (VPT) form.
+// one element per thread (k_cheb_pair_w) or, where the multi-vector form applies,
+// two vectors per lane (k_cheb_pair_wv).
 static bool pair_applies(const gqt_ham* h, int R) {
   if (!h->use_pair || h->variant == 0 || h->threads > 256) return false;
-  if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return false;
-  return !((h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128);
+  return h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6;
+}
+static bool pair_vpt(const gqt_ham* h, int R) {
+  return (h->variant == 2 || h->variant == 3) && R >= 2 && h->threads <= 128;
+}
+
+template <bool FP64, bool CH, int KK>
+static int pair_wv_occupancy_k(int R, int threads) {
+  int n = 0;
+  const void* f = vpt_prefetch<FP64>(KK, R, 2) ? (const void*)k_cheb_pair_wv<FP64, CH, 2, KK, !FP64>
+                                               : (const void*)k_cheb_pair_wv<FP64, CH, 2, KK>;
+  const size_t smem = (size_t)3 * (threads / 32) * R * sizeof(double2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  return std::max(1, n);
+}
+
+template <bool FP64, bool CH>
+static int pair_wv_occupancy(int K, int R, int threads) {
+  switch (K) {
+    case 2: return pair_wv_occupancy_k<FP64, CH, 2>(R, threads);
+    case 3: return pair_wv_occupancy_k<FP64, CH, 3>(R, threads);
+    case 4: return pair_wv_occupancy_k<FP64, CH, 4>(R, threads);
+    default: return pair_wv_occupancy_k<FP64, CH, 6>(R, threads);
+  }
 }
 
 template <bool FP64, bool CH>
@@ -376,7 +402,12 @@ static int moment_grid_per_sm(const gqt_ham* h, int R, int kind) {
   if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return 0;
   const bool dbl = kind == 2;
   int occ;
-  if (kind == 1 && pair_applies(h, R))
+  if (kind == 1 && pair_applies(h, R) && pair_vpt(h, R))
+    occ = h->prec == GQT_FP64 ? (h->hop_real ? pair_wv_occupancy<true, false>(h->K, R, h->threads)
+                                             : pair_wv_occupancy<true, true>(h->K, R, h->threads))
+                              : (h->hop_real ? pair_wv_occupancy<false, false>(h->K, R, h->threads)
+                                             : pair_wv_occupancy<false, true>(h->K, R, h->threads));
+  else if (kind == 1 && pair_applies(h, R))
     occ = h->prec == GQT_FP64 ? (h->hop_real ? pair_occupancy<true, false>(h->K, R, h->threads)
                                              : pair_occupancy<true, true>(h->K, R, h->threads))
                               : (h->hop_real ? pair_occupancy<false, false>(h->K, R, h->threads)
@@ -630,8 +661,16 @@ static void launch_wave_pair(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTabl
   const int4* tab = (const int4*)T.d_tab4.p;
   const size_t sm = smem_bytes(h, R, 3);
 #define GQT_PAIR(KK)                                                                                              \
-  k_cheb_pair_w<FP64, CH, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, am1, bm1, am2, bm2, aout, bout,  \
-                                                                 partial, T.nblocks, m, slot_norm);              \
+  if (pair_vpt(h, R) && vpt_prefetch<FP64>(KK, R, 2))                                                            \
+    k_cheb_pair_wv<FP64, CH, 2, KK, !FP64><<<T.nblocks, h->threads, sm, st>>>(                                   \
+        H, tab, R, rs - 1, am1, bm1, am2, bm2, aout, bout, partial, T.nblocks, m, slot_norm);                    \
+  else if (pair_vpt(h, R))                                                                                       \
+    k_cheb_pair_wv<FP64, CH, 2, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs - 1, am1, bm1, am2, bm2,     \
+                                                                       aout, bout, partial, T.nblocks, m,        \
+                                                                       slot_norm);                               \
+  else                                                                                                           \
+    k_cheb_pair_w<FP64, CH, KK><<<T.nblocks, h->threads, sm, st>>>(H, tab, R, rs, am1, bm1, am2, bm2, aout, bout, \
+                                                                   partial, T.nblocks, m, slot_norm);            \
   break;
   switch (H.K) {
     case 2: GQT_PAIR(2)

@@ -1583,6 +1583,163 @@ __global__ void __launch_bounds__(128, PF ? 5 : 6) k_cheb_dbl_wv(Ell<FP64, CH> H
   write_partials_vpt<FP64, VPT, 2>(v, R, 1 << gs, dyn_smem(), partial, nblocks, slots);
 }
 
+
+// Two-recurrence (l != r) steps in the multi-vector form: the lane layout, the
+// block-uniform loop and the PF prefetch of cheb_wave_vpt, with chain A (from l)
+// and chain B (from r) advanced together; dots and slots as k_cheb_pair_w.
+template <bool FP64, bool CH, int VPT, int KK, bool first, bool PF>
+__device__ __forceinline__ void cheb_pair_vpt(const Ell<FP64, CH>& H, int4 tb, int R, int gs,
+                                              const typename Prec<FP64>::V* __restrict__ am1,
+                                              const typename Prec<FP64>::V* __restrict__ bm1,
+                                              const typename Prec<FP64>::V* am2, const typename Prec<FP64>::V* bm2,
+                                              typename Prec<FP64>::V* aout, typename Prec<FP64>::V* bout,
+                                              DotAcc<typename Prec<FP64>::V> (&d0)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&d1)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&nl)[VPT],
+                                              DotAcc<typename Prec<FP64>::V> (&nr)[VPT]) {
+  using V = typename Prec<FP64>::V;
+  using S = typename Prec<FP64>::S;
+  using HT = typename Ell<FP64, CH>::HT;
+  const size_t gb = (size_t)tb.x << gs, ge = (size_t)tb.y << gs;
+  const size_t step = (size_t)tb.w * blockDim.x;
+  const int G = 1 << gs;
+  const int lg = (int)threadIdx.x & (G - 1);
+  int pidx = 0;
+  HT phop{};
+  auto fetch_next = [&](size_t gn) {
+    if (gn < ge) {
+      const int i = (int)(gn >> gs);
+      if (lg < KK) {
+        const size_t s = (size_t)lg * H.n + i;
+        pidx = __ldg(H.idx + s);
+        phop = __ldg(H.hop2 + s);
+      } else if (lg == KK) {
+        put_re(phop, __ldg(H.diag2 + i));
+      }
+    }
+  };
+  const size_t g_first = gb + (size_t)tb.z * blockDim.x;
+  if (PF) fetch_next(g_first + threadIdx.x);
+  for (size_t g0 = g_first; g0 < ge; g0 += step) {
+    const size_t gi = g0 + threadIdx.x;
+    int idx[KK];
+    HT hv[KK];
+    S dg;
+    if constexpr (PF) {
+      const int cidx = pidx;
+      const HT chop = phop;
+      fetch_next(gi + step);
+#pragma unroll
+      for (int k = 0; k < KK; ++k) {
+        idx[k] = __shfl_sync(0xffffffffu, cidx, k, G);
+        hv[k] = shfl_g(chop, k, G);
+      }
+      dg = get_re(shfl_g(chop, KK, G));
+    }
+    if (gi >= ge) continue;
+    const int i = (int)(gi >> gs);
+    const int r0 = lane_offset<FP64>(lg);
+    const size_t base = (size_t)i * R + r0;
+    if constexpr (!PF) {
+#pragma unroll
+      for (int k = 0; k < KK; ++k) {
+        const size_t s = (size_t)k * H.n + i;
+        idx[k] = __ldg(H.idx + s);
+        hv[k] = __ldg(H.hop2 + s);
+      }
+      dg = __ldg(H.diag2 + i);
+    }
+    V ao[VPT], bo[VPT], a[VPT], b[VPT];
+    ldg_v<VPT>(ao, am1 + base, G);
+    ldg_v<VPT>(bo, bm1 + base, G);
+    if (first) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        a[v] = cscale(ao[v], dg);
+        b[v] = cscale(bo[v], dg);
+      }
+    } else {
+      ld_v<VPT>(a, am2 + base, G);
+      ld_v<VPT>(b, bm2 + base, G);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        a[v] = cmul_acc(cneg(a[v]), dg, ao[v]);
+        b[v] = cmul_acc(cneg(b[v]), dg, bo[v]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+      V na[VPT], nb[VPT];
+      const size_t jb = (size_t)idx[k] * R + r0;
+      ldg_v<VPT>(na, am1 + jb, G);
+      ldg_v<VPT>(nb, bm1 + jb, G);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        a[v] = cmul_acc(a[v], hv[k], na[v]);
+        b[v] = cmul_acc(b[v], hv[k], nb[v]);
+      }
+    }
+    if (first) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        a[v] = cscale(a[v], (S)0.5);
+        b[v] = cscale(b[v], (S)0.5);
+      }
+    }
+    st_v<VPT>(aout + base, a, G);
+    st_v<VPT>(bout + base, b, G);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      d0[v].add_re(ao[v], bo[v]);
+      d1[v].add_re(ao[v], b[v]);
+      if (first) {
+        nl[v].add_norm(ao[v]);
+        nr[v].add_norm(bo[v]);
+      }
+    }
+  }
+}
+
+template <bool FP64, bool CH, int VPT, int KK, bool PF = false>
+__global__ void __launch_bounds__(128, 5) k_cheb_pair_wv(Ell<FP64, CH> H, const int4* __restrict__ tab, int R, int gs,
+                                                         const typename Prec<FP64>::V* __restrict__ am1,
+                                                         const typename Prec<FP64>::V* __restrict__ bm1,
+                                                         const typename Prec<FP64>::V* am2,
+                                                         const typename Prec<FP64>::V* bm2,
+                                                         typename Prec<FP64>::V* aout, typename Prec<FP64>::V* bout,
+                                                         double2* __restrict__ partial, int nblocks, int m,
+                                                         int slot_norm) {
+  using V = typename Prec<FP64>::V;
+  DotAcc<V> d0[VPT], d1[VPT], nl[VPT], nr[VPT];
+  if (m == 1)
+    cheb_pair_vpt<FP64, CH, VPT, KK, true, PF>(H, tab[blockIdx.x], R, gs, am1, bm1, am2, bm2, aout, bout, d0, d1, nl,
+                                               nr);
+  else
+    cheb_pair_vpt<FP64, CH, VPT, KK, false, PF>(H, tab[blockIdx.x], R, gs, am1, bm1, am2, bm2, aout, bout, d0, d1, nl,
+                                                nr);
+  const int G = 1 << gs;
+  if (m == 1) {
+    double2 v[3 * VPT];
+#pragma unroll
+    for (int w = 0; w < VPT; ++w) {
+      v[w] = d0[w].get();
+      v[VPT + w] = d1[w].get();
+      v[2 * VPT + w] = make_double2(nl[w].get().x, nr[w].get().x);
+    }
+    const int slots[3] = {0, 1, slot_norm};
+    write_partials_vpt<FP64, VPT, 3>(v, R, G, dyn_smem(), partial, nblocks, slots);
+  } else {
+    double2 v[2 * VPT];
+#pragma unroll
+    for (int w = 0; w < VPT; ++w) {
+      v[w] = d0[w].get();
+      v[VPT + w] = d1[w].get();
+    }
+    const int slots[2] = {2 * m - 2, 2 * m - 1};
+    write_partials_vpt<FP64, VPT, 2>(v, R, G, dyn_smem(), partial, nblocks, slots);
+  }
+}
+
 }  // namespace gqt
 
 namespace gqt {

@@ -344,7 +344,7 @@ def test_fp64_multivector_tiles_match_oracle(name, R, variant):
 
 @pytest.mark.parametrize("M", [1, 2, 3, 96, 97])
 @pytest.mark.parametrize("name,R", [("honeycomb", 1), ("square_phases", 2), ("chain", 1), ("ragged_honeycomb", 1),
-                                    ("cubic_fp32", 1)])
+                                    ("cubic_fp32", 1), ("cubic_fp32", 8), ("honeycomb_fp32", 16)])
 def test_vac_pair_rows_match_oracle(name, R, M):
     """VAC rows by two recurrences (A_k = T_k l, B_k = T_k r; mu_2k = 2 Re <A_k|B_k> -
     mu_0, mu_2k+1 = 2 Re <A_k|B_k+1> - mu_1) equal the oracle's single-recurrence
@@ -359,6 +359,9 @@ def test_vac_pair_rows_match_oracle(name, R, M):
     elif name == "ragged_honeycomb":
         parts = [S.honeycomb(a, b, -2.7, 1.0, seed=70 + q) for q, (a, b) in enumerate(((7, 3), (11, 9), (4, 4)))]
         dE = S.energy_scale_rule(3, -2.7, 1.0)
+    elif name == "honeycomb_fp32":  # multi-vector form with the next-site prefetch (G = 8 lanes per site)
+        parts = [S.with_random_bond_phases(S.honeycomb(17, 13, -2.7, 1.0, seed=5), 2)]
+        dE, prec = S.energy_scale_rule(3, -2.7, 1.0), g.GQT_FP32_ACC64
     else:
         parts, dE, prec = [S.cubic(13, -1.0, 16.5, seed=6)], S.energy_scale_rule(6, -1.0, 16.5), g.GQT_FP32_ACC64
     lat = parts[0] if len(parts) == 1 else S.block_diagonal(parts)
@@ -380,7 +383,7 @@ def test_vac_pair_rows_match_oracle(name, R, M):
     for q, p in enumerate(parts):
         o = 0 if len(parts) == 1 else lat.seg_offsets[q]
         h = O.Hamiltonian(p, dE)
-        for r in range(R):
+        for r in sorted({0, R // 2, R - 1}):
             ref = h.vac_moments(ph[o:o + p.n, r], dts, Np, M)
             for k in range(len(dts)):
                 assert nerr(got[True][k, q, r], ref[k]) < tol
