@@ -79,6 +79,8 @@ class Lattice:
     displacement along the transport direction taken as the minimum image
     under periodic boundaries (Eq. 34).  ``volume`` is Omega (Eqs. 25-27).
     Slots at or beyond ``nb_count[i]`` hold index i, hopping 0 and dx 0.
+    ``dy`` (optional) is the displacement along the second in-plane direction
+    (Hall responses); it is None for models that do not define it.
     """
 
     name: str
@@ -94,6 +96,7 @@ class Lattice:
     kind: int = 0
     dims: tuple = ()
     seg_offsets: np.ndarray | None = None  # int64 [nseg+1] for block-diagonal batches
+    dy: np.ndarray | None = None  # float64 [N, K], Y_nb - Y_i (minimum image)
 
     def hop_is_real(self) -> bool:
         return bool(np.all(self.hop.imag == 0.0))
@@ -134,7 +137,7 @@ def chain(L: int, t: float = -1.0, W: float = 0.0, seed: int = BASE_SEED, stream
     dx = np.tile(np.array([1.0, -1.0]), (L, 1))
     hop = np.full((L, 2), complex(t), dtype=np.complex128)
     return Lattice("chain", L, 2, np.full(L, 2, np.int32), idx, hop, _onsite(L, W, seed, stream_offset), dx,
-                   float(L), float(L), KIND_CHAIN, (L,))
+                   float(L), float(L), KIND_CHAIN, (L,), dy=np.zeros((L, 2)))
 
 
 def square(Lx: int, Ly: int, t: float = -1.0, W: float = 0.0, seed: int = BASE_SEED, stream_offset: int = 0) -> Lattice:
@@ -148,9 +151,10 @@ def square(Lx: int, Ly: int, t: float = -1.0, W: float = 0.0, seed: int = BASE_S
     idx = np.stack([((ix + 1) % Lx) + Lx * iy, ((ix - 1) % Lx) + Lx * iy,
                     ix + Lx * ((iy + 1) % Ly), ix + Lx * ((iy - 1) % Ly)], axis=1).astype(np.int32)
     dx = np.tile(np.array([1.0, -1.0, 0.0, 0.0]), (n, 1))
+    dy = np.tile(np.array([0.0, 0.0, 1.0, -1.0]), (n, 1))
     hop = np.full((n, 4), complex(t), dtype=np.complex128)
     return Lattice("square", n, 4, np.full(n, 4, np.int32), idx, hop, _onsite(n, W, seed, stream_offset), dx,
-                   float(Lx), float(n), KIND_SQUARE, (Lx, Ly))
+                   float(Lx), float(n), KIND_SQUARE, (Lx, Ly), dy=dy)
 
 
 def cubic(L: int, t: float = -1.0, W: float = 0.0, seed: int = BASE_SEED, stream_offset: int = 0) -> Lattice:
@@ -165,9 +169,10 @@ def cubic(L: int, t: float = -1.0, W: float = 0.0, seed: int = BASE_SEED, stream
                     x + L * ((y + 1) % L) + L * L * z, x + L * ((y - 1) % L) + L * L * z,
                     x + L * y + L * L * ((z + 1) % L), x + L * y + L * L * ((z - 1) % L)], axis=1).astype(np.int32)
     dx = np.tile(np.array([1.0, -1.0, 0.0, 0.0, 0.0, 0.0]), (n, 1))
+    dy = np.tile(np.array([0.0, 0.0, 1.0, -1.0, 0.0, 0.0]), (n, 1))
     hop = np.full((n, 6), complex(t), dtype=np.complex128)
     return Lattice("cubic", n, 6, np.full(n, 6, np.int32), idx, hop, _onsite(n, W, seed, stream_offset), dx,
-                   float(L), float(n), KIND_CUBIC, (L,))
+                   float(L), float(n), KIND_CUBIC, (L,), dy=dy)
 
 
 SQRT3 = math.sqrt(3.0)
@@ -202,13 +207,60 @@ def honeycomb(L1: int, L2: int, t: float = -2.7, W: float = 0.0, seed: int = BAS
     dx = np.empty((n, 3), dtype=np.float64)
     dx[0::2] = [0.0, SQRT3 / 2, -SQRT3 / 2]
     dx[1::2] = [0.0, -SQRT3 / 2, SQRT3 / 2]
+    dy = np.empty((n, 3), dtype=np.float64)
+    dy[0::2] = [1.0, -0.5, -0.5]
+    dy[1::2] = [-1.0, 0.5, 0.5]
     hop = np.full((n, 3), complex(t), dtype=np.complex128)
     lat = Lattice("honeycomb", n, 3, np.full(n, 3, np.int32), idx.astype(np.int32), hop,
                   _onsite(n, W, seed, stream_offset), dx, L1 * SQRT3, ncell * 1.5 * SQRT3,
-                  KIND_HONEYCOMB, (L1, L2))
+                  KIND_HONEYCOMB, (L1, L2), dy=dy)
     if vacancy_frac > 0.0:
         _apply_vacancies(lat, vacancy_sites(n, vacancy_frac, seed, stream_offset))
     return lat
+
+
+def haldane(L1: int, L2: int, t1: float = -1.0, t2: float = 0.15, phi: float = math.pi / 2, mass: float = 0.0,
+            W: float = 0.0, seed: int = BASE_SEED, stream_offset: int = 0) -> Lattice:
+    """Haldane model on the periodic honeycomb lattice of ``honeycomb`` (same
+    cells, site order and nearest-neighbour slots 0-2 with hopping t1), plus six
+    next-nearest-neighbour slots per site with hopping t2*exp(+-i phi): for the
+    vectors d in {a1, a2 - a1, -a2} an A site hops to A(c + d) with exp(+i phi)
+    and to A(c - d) with exp(-i phi); B sites take the opposite signs.  On-site
+    energy +mass on A, -mass on B, plus Anderson disorder W (stream 1).  A
+    Chern insulator for |mass| < 3 sqrt3 |t2 sin phi| (zero net flux per cell).
+    Slots 3-8: +a1, -a1, +(a2-a1), -(a2-a1), -a2, +a2."""
+    if L1 < 3 or L2 < 3:
+        raise ValueError("haldane needs L1, L2 >= 3")
+    base = honeycomb(L1, L2, t1, 0.0)
+    ncell = L1 * L2
+    n = 2 * ncell
+    c = np.arange(ncell, dtype=np.int64)
+    c1, c2 = c % L1, c // L1
+
+    def cell(a, b):
+        return (a % L1) + L1 * (b % L2)
+
+    a1 = np.array([SQRT3, 0.0])
+    a2 = np.array([SQRT3 / 2, 1.5])
+    steps = [((1, 0), +1), ((-1, 0), -1), ((-1, 1), +1), ((1, -1), -1), ((0, -1), +1), ((0, 1), -1)]
+    K = 9
+    idx = np.empty((n, K), np.int64)
+    hop = np.empty((n, K), np.complex128)
+    dx = np.empty((n, K), np.float64)
+    dy = np.empty((n, K), np.float64)
+    idx[:, :3], hop[:, :3], dx[:, :3], dy[:, :3] = base.nb_idx, base.hop, base.dx, base.dy
+    for k, ((e1, e2), sgn) in enumerate(steps):
+        d = e1 * a1 + e2 * a2
+        for s in (0, 1):
+            idx[s::2, 3 + k] = 2 * cell(c1 + e1, c2 + e2) + s
+            hop[s::2, 3 + k] = t2 * np.exp(1j * phi * sgn * (1 if s == 0 else -1))
+            dx[s::2, 3 + k] = d[0]
+            dy[s::2, 3 + k] = d[1]
+    onsite = _onsite(n, W, seed, stream_offset)
+    onsite[0::2] += mass
+    onsite[1::2] -= mass
+    return Lattice("haldane", n, K, np.full(n, K, np.int32), idx.astype(np.int32), hop, onsite, dx,
+                   L1 * SQRT3, ncell * 1.5 * SQRT3, 0, (L1, L2), dy=dy)
 
 
 def block_diagonal(parts: list[Lattice]) -> Lattice:
@@ -220,6 +272,7 @@ def block_diagonal(parts: list[Lattice]) -> Lattice:
     idx = np.zeros((n, K), np.int32)
     hop = np.zeros((n, K), np.complex128)
     dx = np.zeros((n, K), np.float64)
+    dy = np.zeros((n, K), np.float64) if all(p.dy is not None for p in parts) else None
     ons = np.zeros(n, np.float64)
     offs = [0]
     for p in parts:
@@ -230,10 +283,12 @@ def block_diagonal(parts: list[Lattice]) -> Lattice:
         idx[sl, :p.max_nb] = p.nb_idx + o
         hop[sl, :p.max_nb] = p.hop
         dx[sl, :p.max_nb] = p.dx
+        if dy is not None:
+            dy[sl, :p.max_nb] = p.dy
         ons[sl] = p.onsite
         offs.append(o + p.n)
     return Lattice("block_diagonal", n, K, cnt, idx, hop, ons, dx, 0.0, float(sum(p.volume for p in parts)),
-                   0, (), np.array(offs, dtype=np.int64))
+                   0, (), np.array(offs, dtype=np.int64), dy)
 
 
 def ragged_cubic(count: int, lmin: int, lmax: int, t: float, W: float, seed: int) -> Lattice:

@@ -76,6 +76,8 @@ def lib():
             L.orc_cheb_adjoint.argtypes = [C.c_void_p, _d, _d, _d, C.c_int, _d, _d, C.c_void_p]
             L.orc_vac_loss_grad.restype = C.c_double
             L.orc_vac_loss_grad.argtypes = [C.c_void_p, _d, _d, _ip, C.c_int, C.c_int, _d, _d, _d]
+            L.orc_kb_moments.argtypes = [C.c_void_p, _d, _d, _d, C.c_int, C.c_int, _d]
+            L.orc_kubo_bastin.argtypes = [_d, C.c_int, _d, C.c_int, C.c_double, C.c_double, C.c_int, _d]
             _lib = L
     return _lib
 
@@ -196,6 +198,18 @@ class Hamiltonian:
         return J, ge, gs
 
 
+    def kb_moments(self, d_a, d_b, r, M):
+        """Kubo-Bastin moments Lambda_mn = Tr[v~_a T_m(H~) v~_b T_n(H~)] (Hall
+        conductivity, beyond the paper's Sec. 6 outlook) estimated with the unit
+        vectors r [N, R] (site-major); d_a, d_b [N, K] bond displacements of the
+        two directions.  Returns complex [M, M]."""
+        r = np.ascontiguousarray(np.asarray(r, np.complex128).reshape(self.n, -1).T)
+        lam = np.empty((M, M), np.complex128)
+        lib().orc_kb_moments(self._p, np.ascontiguousarray(d_a, np.float64).reshape(-1),
+                             np.ascontiguousarray(d_b, np.float64).reshape(-1), r.view(np.float64).reshape(-1),
+                             r.shape[0], M, lam.view(np.float64).reshape(-1))
+        return lam
+
 def np_rule(x: float, cap: int = 64) -> int:
     """N_p = 1 + max{m : |J_m(x)| >= 1e-15}, capped (Sec. 3.2, machine precision)."""
     return int(lib().orc_np_rule(float(x), int(cap)))
@@ -239,4 +253,15 @@ def sigma_msd(msd, dt):
     dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (msd.shape[0],)))
     out = np.empty_like(msd)
     lib().orc_sigma_msd(msd.reshape(-1), dt, msd.shape[0], msd.shape[1], out.reshape(-1))
+    return out
+
+
+def kubo_bastin(lam, E, energy_scale, area, kernel=0):
+    """sigma_ab(E_j) / (e^2/h) from Kubo-Bastin moments [M, M] on ascending
+    energies E (trapezoid from E_0); kernel 0 = Jackson, 1 = none."""
+    lam = np.ascontiguousarray(lam, np.complex128)
+    E = np.ascontiguousarray(E, np.float64)
+    out = np.empty(E.size, np.float64)
+    lib().orc_kubo_bastin(lam.view(np.float64).reshape(-1), lam.shape[0], E, E.size, float(energy_scale),
+                          float(area), int(kernel), out)
     return out

@@ -70,3 +70,31 @@ def frechet(lam, Q, f, fprime, D):
     """Daleckii-Krein: derivative of f(H) in direction D = Q (F o Q^+ D Q) Q^+."""
     F = divided_difference(lam, f, fprime)
     return Q @ (F * (Q.conj().T @ D @ Q)) @ Q.conj().T
+
+
+def dense_vd(lat, d, scale=1.0):
+    """Velocity along the direction with bond displacements d [N, K] (d = dx or
+    dy), in units of scale/hbar: V_mn = i d_mn H_mn / scale (i [H, X] / scale)."""
+    n = lat.n
+    D = np.zeros((n, n), np.complex128)
+    for i in range(n):
+        for k in range(lat.nb_count[i]):
+            D[i, lat.nb_idx[i, k]] += 1j * d[i, k] * lat.hop[i, k]
+    return D / scale
+
+
+def tknn_sigma(lat, mu_f, da, db):
+    """Zero-temperature Hall conductivity in units of e^2/h from the eigenstates
+    (Kubo formula in the Thouless-Kohmoto-Nightingale-den Nijs form):
+    sigma_ab = (4 pi / Omega) sum_{b occupied} sum_{a != b}
+    Im[<a|v_a|b><b|v_b|a>] / (E_a - E_b)^2, hbar = 1, v = i [H, X]."""
+    H = dense_h(lat)
+    w, Q = np.linalg.eigh(H)
+    va = Q.conj().T @ dense_vd(lat, da) @ Q
+    vb = Q.conj().T @ dense_vd(lat, db) @ Q
+    s = 0.0
+    for b in np.where(w < mu_f)[0]:
+        de = w - w[b]
+        m = np.abs(de) > 1e-9
+        s += np.sum(np.imag(va[m, b] * vb[b, m]) / de[m] ** 2)
+    return 4.0 * np.pi * s / lat.volume

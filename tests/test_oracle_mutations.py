@@ -38,6 +38,13 @@ MUTATIONS = [
      "dt[k - 1] * vac[(int64_t)k * NE + e];"),
     ("adjoint factor 2 dropped", "const double f = (m == 1 ? 1.0 : 2.0) / h.dE;", "const double f = 1.0 / h.dE;"),
     ("adjoint velocity sign", "const cplx mI(0.0, -1.0);", "const cplx mI(0.0, 1.0);"),
+    ("Kubo-Bastin directions swapped", "apply_vd(h, d_a, rq, u.data());", "apply_vd(h, d_b, rq, u.data());"),
+    ("Kubo-Bastin B_n without velocity", "for (int n = 0; n < M; ++n) apply_vd(h, d_b, Tn[n].data(), B[n].data());",
+     "for (int n = 0; n < M; ++n) B[n] = Tn[n];"),
+    ("Kubo-Bastin resolvent phase sign", "std::exp(-I * (double)n * th) * (x + I * (double)n * s)",
+     "std::exp(I * (double)n * th) * (x + I * (double)n * s)"),
+    ("Kubo-Bastin (2 - delta) dropped", "w[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0", "w[n] = (1.0) * (kernel == 0"),
+    ("Kubo-Bastin prefactor 2/Omega", "sigma[j] = 2.0 / area * run;", "sigma[j] = 1.0 / area * run;"),
 ]
 
 PINS = [
@@ -55,6 +62,9 @@ PINS = [
     lambda: P.test_sigma_rules(),
     lambda: P.test_cheb_adjoint_matches_daleckii_krein(),
     lambda: P.test_vac_loss_gradient_matches_finite_differences(),
+    lambda: P.test_kb_moments_match_exact_trace("xy"),
+    lambda: P.test_kb_moments_vanish_by_mirror_symmetry(),
+    lambda: P.test_kubo_bastin_reconstruction_closed_forms(),
 ]
 
 
