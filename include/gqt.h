@@ -89,6 +89,8 @@ typedef struct {
   const double* bond_dx;
   double length_x;
   double volume;
+  const double* bond_dy; /* optional (may be NULL): y displacements [n][max_nb], same
+                            rules as bond_dx; needed only by the Hall moments */
 } gqt_lattice;
 
 typedef struct gqt_ham gqt_ham;
@@ -204,6 +206,34 @@ gqt_status gqt_sigma_vac_loss_weights(int M, const double* d_E, int NE, const do
  * outputs are NaN.  Stream-ordered, asynchronous. */
 gqt_status gqt_bond_gradients(const double* d_g_slot, long long n_slots, const long long* d_slot_a,
                               const long long* d_slot_b, int nbonds, double* d_g_re, double* d_g_im, void* stream);
+
+/* Hall conductivity (Kubo-Bastin formula in the Chebyshev framework; the paper
+ * names it as computable "within the same framework", Sec. 6, after Garcia,
+ * Covaci and Rappoport 2015).  Kubo-Bastin moments
+ *   Lambda_mn = Tr[v~_a T_m(H~) v~_b T_n(H~)],  m, n < M,
+ * with v~ = i d o H~ the velocity along direction a (b) in units of dE/hbar
+ * (d = bond_dx for 0, bond_dy for 1: (v~ x)_i = i sum_k d_ik H~_ik x_j),
+ * estimated from R unit-norm vectors d_r [n][R] (FP64 complex, site-major) as
+ * (N/R) sum_r <T_m v~_a r | v~_b T_n r>.  d_lambda: device FP64 complex
+ * [M][M] (row m, interleaved re, im).  FP64 handles with one segment only;
+ * direction 1 needs a lattice with bond_dy.  Workspace of the handle:
+ * 2 M N R + 3 N R complex vectors (the stacks T_m v~_a r and v~_b T_n r) plus
+ * the split partial sums.  Synchronises the stream before returning. */
+gqt_status gqt_kb_moments(gqt_ham* ham, const void* d_r, int R, int M, int alpha, int beta, double* d_lambda,
+                          void* stream);
+
+/* sigma_ab(E_j) in units of e^2/h at zero temperature from Kubo-Bastin moments:
+ *   sigma(E_j) = (2/area) int_{x_0}^{x_j} dx F(x),  x = E/dE = cos th,
+ *   F(x) = (1 - x^2)^-2 Re sum_mn c_m c_n g_m g_n Gamma_mn(x) Lambda_mn,
+ *   Gamma_mn(x) = T_m(x) e^{-i n th}(x + i n sin th) + T_n(x) e^{i m th}(x - i m sin th),
+ * c_0 = 1, c_n = 2, g_n the Jackson factors (kernel 0; kernel 1: g_n = 1), the
+ * integral by the trapezoid rule over the given energies (so E_0, the lower
+ * limit, belongs below the spectrum and sigma(E_0) = 0).  d_E [NE] ascending
+ * with |E| < dE, d_sigma [NE], d_lambda [M][M] complex: device FP64.  area =
+ * Omega of the 2D sample (hbar = e = 1, lengths of bond_dx/bond_dy).  M <= 8192.
+ * Synchronises the stream before returning. */
+gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale, double area,
+                           int kernel, double* d_sigma, void* stream);
 
 /* Running conductivity from the VAC (Eq. 2): sigma[k][e] = sum_{j<k} dt[j] (v[j][e] + v[j+1][e]) / 2
  * over rows at t_0 = 0 .. t_{Nt-1} of rho*C_vv (device [Nt][NE]); dt host [Nt]. */

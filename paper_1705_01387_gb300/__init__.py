@@ -32,7 +32,7 @@ class gqt_lattice(C.Structure):
                 ("W", C.c_double), ("vacancy_frac", C.c_double), ("seed", C.c_uint64), ("n", C.c_int64),
                 ("max_nb", C.c_int), ("nb_count", C.c_void_p), ("nb_idx", C.c_void_p), ("hop_re", C.c_void_p),
                 ("hop_im", C.c_void_p), ("onsite", C.c_void_p), ("bond_dx", C.c_void_p), ("length_x", C.c_double),
-                ("volume", C.c_double)]
+                ("volume", C.c_double), ("bond_dy", C.c_void_p)]
 
 
 _lib = None
@@ -56,6 +56,8 @@ _SIGS = {
     "gqt_msd_moments": [_P, _P, _P, _I, _P, _P, _I, _I, _P, _P],
     "gqt_kpm_reconstruct": [_P, _I, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kpm_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _P],
+    "gqt_kb_moments": [_P, _P, _I, _I, _I, _I, _P, _P],
+    "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
     "gqt_bond_gradients": [_P, _I64, _P, _P, _I, _P, _P, _P],
     "gqt_sigma_vac": [_P, _P, _I, _I, _P, _P],
@@ -169,6 +171,8 @@ def _lattice_struct(lattice=None, kind=None, L1=0, L2=0, L3=0, t=-1.0, W=0.0, va
                     hop_im=np.ascontiguousarray(np.imag(lattice.hop), np.float64),
                     onsite=np.ascontiguousarray(lattice.onsite, np.float64),
                     bond_dx=np.ascontiguousarray(lattice.dx, np.float64))
+        if getattr(lattice, "dy", None) is not None:
+            arrs["bond_dy"] = np.ascontiguousarray(lattice.dy, np.float64)
         for k, a in arrs.items():
             keep.append(a)
             setattr(s, k, a.ctypes.data)
@@ -314,6 +318,23 @@ def gqt_kpm_weights(M: int, E, w, energy_scale: float, n_over_omega: float, beta
     _check(lib().gqt_kpm_weights(int(M), _dptr(E, "E"), int(E.numel()), _dptr(w, "w"), float(energy_scale),
                                  float(n_over_omega), int(kernel), _dptr(beta, "beta"), _stream(stream)))
     return beta
+
+
+def gqt_kb_moments(ham: Ham, r, R: int, M: int, alpha: int, beta: int, lam, stream=None):
+    """Kubo-Bastin moments Lambda [M, M] (CUDA complex128) of directions alpha, beta
+    (0 = x, 1 = y) from R unit vectors r (CUDA complex128 [N, R])."""
+    _check(lib().gqt_kb_moments(ham.ptr, _dptr(r, "r"), int(R), int(M), int(alpha), int(beta), _dptr(lam, "lam"),
+                                _stream(stream)))
+    return lam
+
+
+def gqt_kubo_bastin(lam, E, energy_scale: float, area: float, sigma, kernel: int = 0, stream=None):
+    """sigma_ab(E) / (e^2/h) (CUDA float64 [NE]) from moments lam (CUDA complex128 [M, M])
+    on ascending energies E (CUDA float64 [NE]; E[0] is the lower integration limit)."""
+    _check(lib().gqt_kubo_bastin(_dptr(lam, "lam"), int(lam.shape[0]), _dptr(E, "E"), int(E.numel()),
+                                 float(energy_scale), float(area), int(kernel), _dptr(sigma, "sigma"),
+                                 _stream(stream)))
+    return sigma
 
 
 def gqt_sigma_vac_loss_weights(M: int, E, w, energy_scale: float, n_over_omega: float, dt, beta, kernel: int = 0,

@@ -37,6 +37,8 @@ struct HostModel {
   int K = 0;
   std::vector<int32_t> cnt, idx;
   std::vector<double> hre, him, eps, dx;
+  std::vector<double> dy;  // second in-plane displacement (Hall responses), when the model defines it
+  bool has_dy = false;
   double length_x = 0, volume = 0;
 };
 
@@ -79,6 +81,8 @@ void gen_lattice(const gqt_lattice& L, HostModel& m) {
     m.hre.assign(n * K, L.t);
     m.him.assign(n * K, 0.0);
     m.dx.assign(n * K, 0.0);
+    m.dy.assign(n * K, 0.0);
+    m.has_dy = true;
   };
   switch (L.kind) {
     case GQT_LATTICE_CHAIN: {
@@ -108,6 +112,8 @@ void gen_lattice(const gqt_lattice& L, HostModel& m) {
         p[3] = (int32_t)(x + Lx * ((y + Ly - 1) % Ly));
         m.dx[4 * s] = 1.0;
         m.dx[4 * s + 1] = -1.0;
+        m.dy[4 * s + 2] = 1.0;
+        m.dy[4 * s + 3] = -1.0;
       }
       m.length_x = (double)Lx;
       m.volume = (double)(Lx * Ly);
@@ -128,6 +134,8 @@ void gen_lattice(const gqt_lattice& L, HostModel& m) {
         p[5] = (int32_t)(x + Q * y + Q * Q * ((z + Q - 1) % Q));
         m.dx[6 * s] = 1.0;
         m.dx[6 * s + 1] = -1.0;
+        m.dy[6 * s + 2] = 1.0;
+        m.dy[6 * s + 3] = -1.0;
       }
       m.length_x = (double)Q;
       m.volume = (double)(Q * Q * Q);
@@ -151,6 +159,13 @@ void gen_lattice(const gqt_lattice& L, HostModel& m) {
         m.dx[3 * A + 2] = -SQ3 / 2;
         m.dx[3 * B + 1] = -SQ3 / 2;
         m.dx[3 * B + 2] = SQ3 / 2;
+        // B sits 1 above A: A -> B(c) is +1 in y, the two other bonds -1/2
+        m.dy[3 * A + 0] = 1.0;
+        m.dy[3 * A + 1] = -0.5;
+        m.dy[3 * A + 2] = -0.5;
+        m.dy[3 * B + 0] = -1.0;
+        m.dy[3 * B + 1] = 0.5;
+        m.dy[3 * B + 2] = 0.5;
       }
       m.length_x = (double)L1 * SQ3;
       m.volume = (double)(L1 * L2) * 1.5 * SQ3;
@@ -175,6 +190,8 @@ void read_custom(const gqt_lattice& L, HostModel& m) {
   m.hre.assign(m.n * m.K, 0.0);
   m.him.assign(m.n * m.K, 0.0);
   m.dx.assign(m.n * m.K, 0.0);
+  m.has_dy = L.bond_dy != nullptr;
+  if (m.has_dy) m.dy.assign(m.n * m.K, 0.0);
   m.eps.assign(m.n, 0.0);
   for (int64_t i = 0; i < m.n; ++i) {
     const int c = L.nb_count[i];
@@ -192,6 +209,7 @@ void read_custom(const gqt_lattice& L, HostModel& m) {
         m.hre[s] = L.hop_re ? L.hop_re[so] : -1.0;
         m.him[s] = L.hop_im ? L.hop_im[so] : 0.0;
         m.dx[s] = L.bond_dx[so];
+        if (m.has_dy) m.dy[s] = L.bond_dy[so];
       } else {
         m.idx[s] = (int32_t)i;
       }
@@ -211,8 +229,9 @@ void validate(HostModel& m, const std::vector<int64_t>& seg) {
   for (int64_t i = 0; i < m.n; ++i) {
     for (int k = 0; k < m.cnt[i]; ++k) {
       const int64_t s = i * m.K + k;
-      if (!std::isfinite(m.hre[s]) || !std::isfinite(m.him[s]) || !std::isfinite(m.dx[s]))
-        throw Error(GQT_ENAN, "non-finite hopping or dx in row " + std::to_string(i));
+      if (!std::isfinite(m.hre[s]) || !std::isfinite(m.him[s]) || !std::isfinite(m.dx[s]) ||
+          (m.has_dy && !std::isfinite(m.dy[s])))
+        throw Error(GQT_ENAN, "non-finite hopping or displacement in row " + std::to_string(i));
       const int64_t j = m.idx[s];
       if (site_seg[j] != site_seg[i])
         throw Error(GQT_EINVAL, "bond " + std::to_string(i) + "-" + std::to_string(j) + " crosses a segment boundary");
@@ -223,7 +242,8 @@ void validate(HostModel& m, const std::vector<int64_t>& seg) {
         const int64_t t = j * m.K + kk;
         if (m.idx[t] != i) continue;
         if (std::fabs(m.hre[t] - m.hre[s]) <= tol && std::fabs(m.him[t] + m.him[s]) <= tol &&
-            std::fabs(m.dx[t] + m.dx[s]) <= 1e-12 * (1.0 + std::fabs(m.dx[s])))
+            std::fabs(m.dx[t] + m.dx[s]) <= 1e-12 * (1.0 + std::fabs(m.dx[s])) &&
+            (!m.has_dy || std::fabs(m.dy[t] + m.dy[s]) <= 1e-12 * (1.0 + std::fabs(m.dy[s]))))
           ok = true;
       }
       if (!ok)
@@ -349,6 +369,14 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
       upload(h->d_hop, hop.data(), hop.size() * 4);
       upload(h->d_diag, dg.data(), dg.size() * 4);
       upload(h->d_dx, dxv.data(), dxv.size() * 4);
+    }
+    // y displacements (FP64, slot-major) for the Hall moments
+    h->has_dy = m.has_dy;
+    if (m.has_dy) {
+      std::vector<double> dyv(n * K);
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = 0; k < K; ++k) dyv[k * n + i] = m.dy[i * K + k];
+      upload(h->d_dy, dyv.data(), dyv.size() * 8);
     }
     if (nseg > 1) {
       std::vector<int32_t> ss(n);

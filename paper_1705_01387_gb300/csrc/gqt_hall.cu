@@ -1,0 +1,430 @@
+// gqt_hall.cu -- Hall conductivity by the Kubo-Bastin formula in the Chebyshev
+// framework of the library (the paper's outlook, Sec. 6, after Garcia, Covaci
+// and Rappoport 2015).
+//
+//   Lambda_mn = Tr[v~_a T_m(H~) v~_b T_n(H~)],  v~ = i d o H~ (velocity along
+//   the direction with bond displacements d, in units of dE/hbar), estimated
+//   with R unit random vectors r as (N/R) sum_r <P_m|B_n>,
+//   P_m = T_m(H~) v~_a r,  B_n = v~_b T_n(H~) r;
+//
+//   sigma_ab(mu)/(e^2/h) = (2/Omega) int dx (1 - x^2)^-2 Re sum_mn c_m c_n g_m g_n
+//   Gamma_mn(x) Lambda_mn,  Gamma_mn(x) = T_m(x) e^{-i n th}(x + i n sin th)
+//   + T_n(x) e^{i m th}(x - i m sin th),  x = cos th.
+//
+// Three kernels carry the work.  k_kb_step advances both Chebyshev chains one
+// order and applies v~_b to T_k r from the same neighbour gathers, writing the
+// stacks P (M vectors) and B (M vectors).  k_kb_gemm forms all M x M inner
+// products <P_m|B_n> -- a dense complex contraction over N*R, the dominant cost
+// (4 M^2 N R FP64 FMAs) -- as a register-blocked FP64 GEMM with a deterministic
+// split over the contraction.  k_kb_integrand evaluates the double sum on an
+// energy grid (a bilinear form per energy), and k_kb_scan integrates it.
+
+#include <cuda_runtime.h>
+
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "gqt_internal.h"
+
+using gqt::check_cuda;
+using gqt::check_launch;
+using gqt::Error;
+using gqt::set_error;
+
+namespace {
+
+enum { WS_HALL_P = 40, WS_HALL_B, WS_HALL_Q, WS_HALL_PART, WS_HALL_F, WS_HALL_W };
+
+template <bool CH>
+struct HallEll {
+  using HT = typename std::conditional<CH, double2, double>::type;
+  int64_t n;
+  int K;
+  const int* __restrict__ idx;  // slot-major [K][n]
+  const HT* __restrict__ hop2;  // 2 H~ per slot
+  const double* __restrict__ diag2;
+};
+
+__device__ __forceinline__ double2 mla(double2 acc, double h, double2 x) {
+  acc.x = fma(h, x.x, acc.x);
+  acc.y = fma(h, x.y, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 mla(double2 acc, double2 h, double2 x) {
+  acc.x = fma(h.x, x.x, acc.x);
+  acc.x = fma(-h.y, x.y, acc.x);
+  acc.y = fma(h.x, x.y, acc.y);
+  acc.y = fma(h.y, x.x, acc.y);
+  return acc;
+}
+
+// y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2).
+template <bool CH>
+__global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R, size_t total,
+                              const double2* __restrict__ x, double2* __restrict__ y) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / R;
+    const int r = (int)(e - i * R);
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < H.K; ++k) {
+      const size_t sl = (size_t)k * H.n + i;
+      const double2 xj = x[(size_t)H.idx[sl] * R + r];
+      s = mla(s, H.hop2[sl], make_double2(d[sl] * xj.x, d[sl] * xj.y));
+    }
+    y[e] = make_double2(-0.5 * s.y, 0.5 * s.x);
+  }
+}
+
+// Order k of both chains, element e = i*R + r:
+//   P_{k+1} = 2H~P_k - P_{k-1}   (P_1 = H~P_0 at k = 0), unless last
+//   Q_{k+1} = 2H~Q_k - Q_{k-1}   (Q_1 = H~Q_0),           unless last
+//   B_k = v~_b Q_k                (from the same gathers of Q_k)
+template <bool CH>
+__global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __restrict__ db, int R, size_t total,
+                                                 const double2* __restrict__ pk, const double2* __restrict__ pkm1,
+                                                 double2* __restrict__ pout, const double2* __restrict__ qk,
+                                                 const double2* __restrict__ qkm1, double2* __restrict__ qout,
+                                                 double2* __restrict__ bout, int first, int last) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / R;
+    const int r = (int)(e - i * R);
+    const double dg = H.diag2[i];
+    double2 a = make_double2(0.0, 0.0), q = a, b = a;
+    for (int k = 0; k < H.K; ++k) {
+      const size_t sl = (size_t)k * H.n + i;
+      const size_t j = (size_t)H.idx[sl] * R + r;
+      const auto h2 = H.hop2[sl];
+      const double2 qj = qk[j];
+      q = mla(q, h2, qj);
+      b = mla(b, h2, make_double2(db[sl] * qj.x, db[sl] * qj.y));
+      if (!last) a = mla(a, h2, pk[j]);
+    }
+    bout[e] = make_double2(-0.5 * b.y, 0.5 * b.x);
+    if (last) continue;
+    a = mla(a, dg, pk[e]);
+    q = mla(q, dg, qk[e]);
+    if (first) {
+      pout[e] = make_double2(0.5 * a.x, 0.5 * a.y);
+      qout[e] = make_double2(0.5 * q.x, 0.5 * q.y);
+    } else {
+      const double2 p0 = pkm1[e], q0 = qkm1[e];
+      pout[e] = make_double2(a.x - p0.x, a.y - p0.y);
+      qout[e] = make_double2(q.x - q0.x, q.y - q0.y);
+    }
+  }
+}
+
+// part[s][m][n] = sum_{k in split s} conj(P[m][k]) B[n][k], P and B row-major
+// [M][Kt].  64 x 64 output tile per CTA, 4 x 4 complex outputs per thread
+// (rows tm + 16 i, columns tn + 16 j), contraction chunks of 16 staged in
+// shared memory (columns padded by one element against bank conflicts).
+constexpr int KB_TM = 64, KB_TK = 16;
+
+__global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ P, const double2* __restrict__ B, int M,
+                                                    size_t Kt, size_t kchunk, double2* __restrict__ part) {
+  __shared__ double2 Ps[KB_TK][KB_TM + 1];
+  __shared__ double2 Bs[KB_TK][KB_TM + 1];
+  const int m0 = blockIdx.x * KB_TM, n0 = blockIdx.y * KB_TM;
+  const size_t kb = (size_t)blockIdx.z * kchunk;
+  const size_t ke = (kb + kchunk < Kt) ? kb + kchunk : Kt;
+  const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = make_double2(0.0, 0.0);
+  for (size_t k0 = kb; k0 < ke; k0 += KB_TK) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int q = tid + 256 * p;
+      const int row = q >> 4, kk = q & 15;
+      const size_t k = k0 + kk;
+      const bool kin = k < ke;
+      Ps[kk][row] = (kin && m0 + row < M) ? P[(size_t)(m0 + row) * Kt + k] : make_double2(0.0, 0.0);
+      Bs[kk][row] = (kin && n0 + row < M) ? B[(size_t)(n0 + row) * Kt + k] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KB_TK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = Ps[kk][tm + 16 * u];
+        b[u] = Bs[kk][tn + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v].x = fma(a[u].x, b[v].x, acc[u][v].x);
+          acc[u][v].x = fma(a[u].y, b[v].y, acc[u][v].x);
+          acc[u][v].y = fma(a[u].x, b[v].y, acc[u][v].y);
+          acc[u][v].y = fma(-a[u].y, b[v].x, acc[u][v].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int m = m0 + tm + 16 * u, nn = n0 + tn + 16 * v;
+      if (m < M && nn < M) part[((size_t)blockIdx.z * M + m) * M + nn] = acc[u][v];
+    }
+}
+
+// lam[m][n] = scale * sum_s part[s][m][n], splits summed in order (deterministic).
+__global__ void k_kb_reduce(const double2* __restrict__ part, int S, int M, double scale, double2* __restrict__ lam) {
+  const size_t total = (size_t)M * M;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < S; ++q) {
+      const double2 v = part[(size_t)q * total + t];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    lam[t] = make_double2(scale * s.x, scale * s.y);
+  }
+}
+
+// F(x_e) = (1 - x^2)^-2 Re sum_mn Gamma_mn(x) W_mn Lambda_mn for EB energies per
+// CTA, W_mn = w_m w_n (w = c_n g_n).  Per energy the sum is
+//   sum_m Tw_m z1_m + conj(aw_m) z2_m,  z1_m = sum_n Lambda_mn aw_n,  z2_m = sum_n Lambda_mn Tw_n,
+// Tw_n = w_n T_n(x), aw_n = w_n e^{-i n th}(x + i n sin th) (and w_m e^{i m th}(x - i m sin th)
+// = conj(aw_m)).  Tables in shared memory; one warp per row m, lanes over n.
+template <int EB>
+__global__ void __launch_bounds__(256) k_kb_integrand(const double2* __restrict__ lam, int M,
+                                                      const double* __restrict__ E, int NE, double inv_dE,
+                                                      const double* __restrict__ w, double* __restrict__ F) {
+  extern __shared__ double kb_sm[];
+  double2* aw = reinterpret_cast<double2*>(kb_sm);  // [EB][M], first: 16-byte aligned for any M
+  double* Tw = kb_sm + 2 * EB * M;                   // [EB][M]
+  __shared__ double2 red[EB][8];
+  const int e0 = blockIdx.x * EB;
+  for (int t = threadIdx.x; t < EB * M; t += blockDim.x) {
+    const int e = t / M, n = t - e * M;
+    double x = 0.0;
+    if (e0 + e < NE) x = E[e0 + e] * inv_dE;
+    const double th = acos(x), s = sin(th);
+    double sn, cn;
+    sincos((double)n * th, &sn, &cn);
+    Tw[t] = w[n] * cn;
+    // e^{-i n th}(x + i n s) = (cn - i sn)(x + i n s)
+    aw[t] = make_double2(w[n] * (cn * x + sn * n * s), w[n] * (cn * n * s - sn * x));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double2 acc[EB];
+#pragma unroll
+  for (int e = 0; e < EB; ++e) acc[e] = make_double2(0.0, 0.0);
+  for (int m = warp; m < M; m += nw) {
+    double2 z1[EB], z2[EB];
+#pragma unroll
+    for (int e = 0; e < EB; ++e) z1[e] = z2[e] = make_double2(0.0, 0.0);
+    const double2* row = lam + (size_t)m * M;
+    for (int nn = lane; nn < M; nn += 32) {
+      const double2 l = row[nn];
+#pragma unroll
+      for (int e = 0; e < EB; ++e) {
+        const double2 a = aw[e * M + nn];
+        const double t = Tw[e * M + nn];
+        z1[e].x = fma(l.x, a.x, fma(-l.y, a.y, z1[e].x));
+        z1[e].y = fma(l.x, a.y, fma(l.y, a.x, z1[e].y));
+        z2[e].x = fma(l.x, t, z2[e].x);
+        z2[e].y = fma(l.y, t, z2[e].y);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      for (int off = 16; off > 0; off >>= 1) {
+        z1[e].x += __shfl_xor_sync(0xffffffffu, z1[e].x, off);
+        z1[e].y += __shfl_xor_sync(0xffffffffu, z1[e].y, off);
+        z2[e].x += __shfl_xor_sync(0xffffffffu, z2[e].x, off);
+        z2[e].y += __shfl_xor_sync(0xffffffffu, z2[e].y, off);
+      }
+      if (lane == 0) {
+        const double tm = Tw[e * M + m];
+        const double2 am = aw[e * M + m];  // conj(am) multiplies z2
+        acc[e].x += tm * z1[e].x + am.x * z2[e].x + am.y * z2[e].y;
+        acc[e].y += tm * z1[e].y + am.x * z2[e].y - am.y * z2[e].x;
+      }
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int e = 0; e < EB; ++e) red[e][warp] = acc[e];
+  __syncthreads();
+  if ((int)threadIdx.x < EB && e0 + (int)threadIdx.x < NE) {
+    const int e = threadIdx.x;
+    double s = 0.0;
+    for (int q = 0; q < nw; ++q) s += red[e][q].x;
+    const double x = E[e0 + e] * inv_dE;
+    F[e0 + e] = s / ((1.0 - x * x) * (1.0 - x * x));
+  }
+}
+
+// sigma_j = pref * sum_{k<j} (x_{k+1} - x_k)(F_k + F_{k+1})/2 (one thread: a running sum).
+__global__ void k_kb_scan(const double* __restrict__ F, const double* __restrict__ E, int NE, double inv_dE,
+                          double pref, double* __restrict__ sigma) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double run = 0.0;
+  for (int j = 0; j < NE; ++j) {
+    if (j > 0) run += 0.5 * (E[j] - E[j - 1]) * inv_dE * (F[j] + F[j - 1]);
+    sigma[j] = pref * run;
+  }
+}
+
+double jackson_g(int n, int M) {
+  const double a = 1.0 / (M + 1.0), pi = 3.14159265358979323846;
+  return (1.0 - n * a) * std::cos(pi * n * a) + a * std::sin(pi * n * a) / std::tan(pi * a);
+}
+
+int grid_for(size_t total) {
+  const size_t want = (total + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)gqt::sm_count() * 8));
+}
+
+template <bool CH>
+void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* da, const double* db, double2* lam,
+                     cudaStream_t st) {
+  HallEll<CH> H;
+  H.n = h->n;
+  H.K = h->K;
+  H.idx = (const int*)h->d_idx.p;
+  H.hop2 = (const typename HallEll<CH>::HT*)h->d_hop.p;
+  H.diag2 = (const double*)h->d_diag.p;
+  const size_t total = (size_t)h->n * R;
+  const size_t vb = total * sizeof(double2);
+  double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
+  double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
+  double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
+  const int g = grid_for(total);
+  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst);
+  check_launch("k_kb_velocity");
+  auto qbuf = [&](int k) -> double2* { return Q + (size_t)(k % 3) * total; };
+  for (int k = 0; k < M; ++k) {
+    const bool last = k == M - 1;
+    const double2* qk = k == 0 ? r : qbuf(k);
+    const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
+    k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
+                                      k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
+                                      last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
+                                      last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last);
+    check_launch("k_kb_step");
+  }
+  // split of the contraction: about eight waves of two resident CTAs per SM, at
+  // least 512 contraction elements per split
+  const int tiles = (M + KB_TM - 1) / KB_TM;
+  const long long slots = 2LL * gqt::sm_count();
+  long long S = std::max<long long>(1, (8 * slots + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
+  S = std::min<long long>(S, std::max<long long>(1, (long long)(total / 512)));
+  const size_t kchunk = ((total + S - 1) / S + KB_TK - 1) / KB_TK * KB_TK;
+  S = (long long)((total + kchunk - 1) / kchunk);
+  double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * M * M * sizeof(double2)).p;
+  k_kb_gemm<<<dim3(tiles, tiles, (unsigned)S), 256, 0, st>>>(Pst, Bst, M, total, kchunk, part);
+  check_launch("k_kb_gemm");
+  const size_t mm = (size_t)M * M;
+  k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M,
+                                                                              (double)h->n / R, lam);
+  check_launch("k_kb_reduce");
+}
+
+}  // namespace
+
+extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, int alpha, int beta,
+                                     double* d_lambda, void* stream) {
+  try {
+    if (!h || !d_r || !d_lambda || R < 1 || M < 1 || alpha < 0 || alpha > 1 || beta < 0 || beta > 1)
+      throw Error(GQT_EINVAL, "gqt_kb_moments: bad argument");
+    if (h->prec != GQT_FP64) throw Error(GQT_EINVAL, "gqt_kb_moments: needs an FP64 handle");
+    if (h->nseg != 1) throw Error(GQT_EINVAL, "gqt_kb_moments: one segment only");
+    if ((alpha == 1 || beta == 1) && !h->has_dy)
+      throw Error(GQT_EINVAL, "gqt_kb_moments: the lattice has no y displacements (bond_dy)");
+    check_cuda(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* d[2] = {(const double*)h->d_dx.p, (const double*)h->d_dy.p};
+    if (h->hop_real)
+      kb_moments_impl<false>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
+    else
+      kb_moments_impl<true>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
+    check_cuda(cudaStreamSynchronize(st), "gqt_kb_moments");
+    return GQT_OK;
+  } catch (const Error& e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return GQT_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(std::string("internal error: ") + e.what());
+    return GQT_ECUDA;
+  }
+}
+
+extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,
+                                      double area, int kernel, double* d_sigma, void* stream) {
+  try {
+    if (!d_lambda || !d_E || !d_sigma || M < 1 || M > 8192 || NE < 1 || !(energy_scale > 0) || !(area > 0) ||
+        kernel < 0 || kernel > 1)
+      throw Error(GQT_EINVAL, "gqt_kubo_bastin: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> hE(NE);
+    check_cuda(cudaMemcpyAsync(hE.data(), d_E, NE * sizeof(double), cudaMemcpyDeviceToHost, st), "energies");
+    check_cuda(cudaStreamSynchronize(st), "energies");
+    for (int j = 0; j < NE; ++j) {
+      if (!(std::fabs(hE[j]) < energy_scale)) throw Error(GQT_EINVAL, "gqt_kubo_bastin: |E| must be < dE");
+      if (j > 0 && !(hE[j] > hE[j - 1])) throw Error(GQT_EINVAL, "gqt_kubo_bastin: energies must ascend");
+    }
+    std::vector<double> hw(M);
+    for (int n = 0; n < M; ++n) hw[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0 ? jackson_g(n, M) : 1.0);
+    // energies per CTA: as many as keep the tables (24 B per energy and moment) within 200 KB
+    const int EB = (size_t)4 * M * 24 <= 200 * 1024 ? 4 : ((size_t)2 * M * 24 <= 200 * 1024 ? 2 : 1);
+    const size_t smem = (size_t)EB * M * (sizeof(double) + sizeof(double2));
+    const void* kern = EB == 4 ? (const void*)k_kb_integrand<4>
+                               : (EB == 2 ? (const void*)k_kb_integrand<2> : (const void*)k_kb_integrand<1>);
+    if (smem > 48 * 1024)
+      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute");
+    // device scratch owned by this call (no handle): weights and F
+    double* buf = nullptr;
+    check_cuda(cudaMallocAsync((void**)&buf, (size_t)(M + NE) * sizeof(double), st), "cudaMallocAsync");
+    double* w = buf;
+    double* F = buf + M;
+    const double inv = 1.0 / energy_scale;
+    cudaError_t err = cudaMemcpyAsync(w, hw.data(), M * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) {
+      const dim3 grid((NE + EB - 1) / EB);
+      const double2* lam = (const double2*)d_lambda;
+      if (EB == 4)
+        k_kb_integrand<4><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+      else if (EB == 2)
+        k_kb_integrand<2><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+      else
+        k_kb_integrand<1><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+      err = cudaGetLastError();
+      if (err == cudaSuccess) {
+        check_launch("k_kb_integrand");
+        k_kb_scan<<<1, 32, 0, st>>>(F, d_E, NE, inv, 2.0 / area, d_sigma);
+        err = cudaGetLastError();
+        if (err == cudaSuccess) check_launch("k_kb_scan");
+      }
+    }
+    cudaFreeAsync(buf, st);
+    check_cuda(err, "gqt_kubo_bastin");
+    check_cuda(cudaStreamSynchronize(st), "gqt_kubo_bastin");
+    return GQT_OK;
+  } catch (const Error& e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return GQT_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(std::string("internal error: ") + e.what());
+    return GQT_ECUDA;
+  }
+}

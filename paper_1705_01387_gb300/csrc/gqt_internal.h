@@ -80,6 +80,8 @@ struct gqt_ham {
   int nseg = 1;
   std::vector<int64_t> seg;  // nseg + 1 offsets
   gqt::DevBuf d_idx, d_hop, d_diag, d_dx, d_site_seg, d_flag;
+  gqt::DevBuf d_dy;     // FP64 slot-major y displacements (Hall moments), when the model defines them
+  bool has_dy = false;
   int* h_flag = nullptr;  // pinned
   int threads = 256;
   int blocks_per_sm = 0;
