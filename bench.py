@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -582,6 +583,71 @@ def _oracle_sample(small: bool):
     return w, lat, h, phi
 
 
+def hall(args, g, torch):
+    """Hall conductivity (Kubo-Bastin; the paper's Sec. 6 outlook) of the
+    disordered Haldane model: honeycomb 512 x 512 cells (N = 524,288), t1 = -1,
+    t2 = 0.15, phi = pi/2, Anderson W = 1, one random-phase vector, M = 1024
+    Kubo-Bastin moments, sigma_xy on 2001 energies.  Times gqt_kb_moments (the
+    two chains plus the M x M complex contraction) and gqt_kubo_bastin with CUDA
+    events; per-kernel times from the library's profiler (families 7-9)."""
+    L = args.hall_L or (32 if args.small else 512)
+    M = args.hall_moments or (128 if args.small else 1024)
+    seed = 1705013875
+    lat = S.haldane(L, L, -1.0, 0.15, math.pi / 2, 0.0, 1.0, seed=seed)
+    dE = 1.05 * (3 + 6 * 0.15 + 0.5)
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    r = torch.from_numpy(S.random_phase(lat.n, 1, seed=seed)).cuda()
+    lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+    E = torch.linspace(-0.97 * dE, 0.97 * dE, 2001, dtype=torch.float64, device="cuda")
+    sig = torch.empty_like(E)
+    for _ in range(max(1, args.warmup)):
+        g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+        g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    g.gqt_profile_start()
+    ev[0].record()
+    for _ in range(steps):
+        g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+    ev[1].record()
+    for _ in range(steps):
+        g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
+    ev[2].record()
+    torch.cuda.synchronize()
+    prof_ms, prof_n = g.gqt_profile_stop(10)
+    t_mom = ev[0].elapsed_time(ev[1]) * 1e-3 / steps
+    t_kb = ev[1].elapsed_time(ev[2]) * 1e-3 / steps
+    n = lat.n
+    gemm_s = prof_ms[8] * 1e-3 / max(int(prof_n[8]), 1)
+    fma = 4.0 * M * M * n
+    fp64_peak = g.gqt_probe_fp64()
+    s_np = sig.cpu().numpy()
+    e_np = E.cpu().numpy()
+    i0 = int(np.argmin(np.abs(e_np)))
+    out = {"workload": f"haldane{L}x{L}_W1_M{M}", "n_orbitals": n, "moments": M, "vectors": 1,
+           "metric": "Kubo-Bastin orbital-moment pairs/s (N R M^2 / time of gqt_kb_moments)",
+           "value": n * M * M / t_mom, "kb_moments_s": t_mom, "kubo_bastin_s": t_kb, "energies": int(E.numel()),
+           "kernels": {"k_kb_step_ms_per_launch": prof_ms[7] / max(int(prof_n[7]), 1), "k_kb_step_launches": int(prof_n[7]) // steps,
+                       "k_kb_gemm_ms": gemm_s * 1e3, "k_kb_integrand_ms": prof_ms[9] / max(int(prof_n[9]), 1)},
+           "roofline": {"kernel": "k_kb_gemm (M x M complex FP64 contraction over N)", "bound": "alu",
+                        "achieved": 2 * fma / gemm_s / 1e9, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                        "frac": 2 * fma / gemm_s / 1e9 / fp64_peak, "fp64_fma": fma,
+                        "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)"},
+           "sigma_xy_gap_centre_e2_over_h": float(s_np[i0]), "sigma_xy_energy": float(e_np[i0])}
+    if not args.no_cpu_baseline:
+        import oracle as O  # the CPU baseline leg only
+        h = O.Hamiltonian(lat, dE)
+        Mc = 24
+        t0 = time.perf_counter()
+        h.kb_moments(lat.dx, lat.dy, r.cpu().numpy(), Mc)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n * Mc * Mc / dt, "unit": "orbital-moment pairs/s", "cores": 1,
+                               "kind": "oracle", "sample": f"oracle Kubo-Bastin moments, M = {Mc} at full N = {n} "
+                                                           f"(serial FP64 C++, {dt:.1f} s)"}
+    return out
+
+
 def cpu_baseline(small: bool, budget_s: float = 15.0, prepared=None):
     """Serial FP64 oracle on one host core: Chebyshev moments at full N, as many
     as fit in about budget_s seconds, scaled to orbital-moments/s."""
@@ -646,9 +712,16 @@ def main():
     ap.add_argument("--latency", action="store_true", help="latency-bound workloads (C1 graphs on/off, C5 gradient)")
     ap.add_argument("--paper-examples", action="store_true", help="the paper's two examples (Sec. 5), timed")
     ap.add_argument("--precision-steps", type=int, default=3, help="VAC/MSD time steps of the error table")
+    ap.add_argument("--hall", action="store_true", help="Hall conductivity (Kubo-Bastin) of the Haldane model")
+    ap.add_argument("--hall-L", type=int, default=0, help="Haldane cells per side of the Hall run (profiling)")
+    ap.add_argument("--hall-moments", type=int, default=0, help="Kubo-Bastin moments of the Hall run (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.hall:
+        import torch
+        import paper_1705_01387_gb300 as g
+        print(json.dumps(hall(args, g, torch)))
     elif args.paper_examples:
         import torch
         import paper_1705_01387_gb300 as g

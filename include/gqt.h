@@ -316,7 +316,9 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
  * m >= 2 with l != r (the fused SpMV + recurrence + dot kernel), 2 = one-set
  * evolution order, 3 = two-set evolution order, 4 = coupled commutator order,
  * 5 = moment steps m >= 2 with l = r (two moments per step), 6 = moment steps
- * m >= 2 of the two-recurrence l != r rows (two moments per step).  Graph
+ * m >= 2 of the two-recurrence l != r rows (two moments per step), 7 = Hall
+ * chain orders (gqt_kb_moments), 8 = Hall moment contraction (the M x M
+ * complex GEMM), 9 = Kubo-Bastin energy sums (gqt_kubo_bastin).  Graph
  * capture is bypassed while profiling. */
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);

@@ -33,6 +33,8 @@
 
 using gqt::check_cuda;
 using gqt::check_launch;
+using gqt::prof_begin;
+using gqt::prof_end;
 using gqt::Error;
 using gqt::set_error;
 
@@ -311,11 +313,13 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     const bool last = k == M - 1;
     const double2* qk = k == 0 ? r : qbuf(k);
     const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
+    const size_t pe = prof_begin(st);
     k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
                                       k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
                                       last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
                                       last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last);
     check_launch("k_kb_step");
+    prof_end(pe, 7, st);
   }
   // split of the contraction: about eight waves of two resident CTAs per SM, at
   // least 512 contraction elements per split
@@ -326,8 +330,10 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   const size_t kchunk = ((total + S - 1) / S + KB_TK - 1) / KB_TK * KB_TK;
   S = (long long)((total + kchunk - 1) / kchunk);
   double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * M * M * sizeof(double2)).p;
+  const size_t pg = prof_begin(st);
   k_kb_gemm<<<dim3(tiles, tiles, (unsigned)S), 256, 0, st>>>(Pst, Bst, M, total, kchunk, part);
   check_launch("k_kb_gemm");
+  prof_end(pg, 8, st);
   const size_t mm = (size_t)M * M;
   k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M,
                                                                               (double)h->n / R, lam);
@@ -399,6 +405,7 @@ extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const doubl
     if (err == cudaSuccess) {
       const dim3 grid((NE + EB - 1) / EB);
       const double2* lam = (const double2*)d_lambda;
+      const size_t pi = prof_begin(st);
       if (EB == 4)
         k_kb_integrand<4><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
       else if (EB == 2)
@@ -408,6 +415,7 @@ extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const doubl
       err = cudaGetLastError();
       if (err == cudaSuccess) {
         check_launch("k_kb_integrand");
+        prof_end(pi, 9, st);
         k_kb_scan<<<1, 32, 0, st>>>(F, d_E, NE, inv, 2.0 / area, d_sigma);
         err = cudaGetLastError();
         if (err == cudaSuccess) check_launch("k_kb_scan");

@@ -154,13 +154,13 @@ struct Profiler {
 Profiler g_prof;
 }  // namespace
 
-static inline size_t prof_begin(cudaStream_t st) {
+size_t gqt::prof_begin(cudaStream_t st) {
   if (!g_prof.on) return (size_t)-1;
   size_t i = g_prof.used;
   check_cuda(cudaEventRecord(g_prof.get(), st), "cudaEventRecord");
   return i;
 }
-static inline void prof_end(size_t i, int cat, cudaStream_t st) {
+void gqt::prof_end(size_t i, int cat, cudaStream_t st) {
   if (i == (size_t)-1) return;
   check_cuda(cudaEventRecord(g_prof.get(), st), "cudaEventRecord");
   g_prof.pairs.push_back({cat, i});

@@ -20,6 +20,9 @@ struct Error : std::runtime_error {
 };
 
 void set_error(const std::string& s);
+// Per-kernel timing (gqt_profile_start/stop): events around a launch of family cat.
+size_t prof_begin(cudaStream_t st);
+void prof_end(size_t i, int cat, cudaStream_t st);
 void check_cuda(cudaError_t e, const char* what);
 void check_launch(const char* what);
 int sm_count();
