@@ -588,7 +588,8 @@ def hall(args, g, torch):
     disordered Haldane model: honeycomb 512 x 512 cells (N = 524,288), t1 = -1,
     t2 = 0.15, phi = pi/2, Anderson W = 1, one random-phase vector, M = 1024
     Kubo-Bastin moments, sigma_xy on 2001 energies.  Times gqt_kb_moments (the
-    two chains plus the M x M complex contraction) and gqt_kubo_bastin with CUDA
+    two chains plus the M x M complex contraction) with the FP64 contraction and
+    with the split-TF32 tensor-core contraction, and gqt_kubo_bastin, with CUDA
     events; per-kernel times from the library's profiler (families 7-9)."""
     L = args.hall_L or (32 if args.small else 512)
     M = args.hall_moments or (128 if args.small else 1024)
@@ -597,44 +598,66 @@ def hall(args, g, torch):
     dE = 1.05 * (3 + 6 * 0.15 + 0.5)
     ham = g.gqt_build_hamiltonian(lat, dE)
     r = torch.from_numpy(S.random_phase(lat.n, 1, seed=seed)).cuda()
-    lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
     E = torch.linspace(-0.97 * dE, 0.97 * dE, 2001, dtype=torch.float64, device="cuda")
-    sig = torch.empty_like(E)
-    for _ in range(max(1, args.warmup)):
-        g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
-        g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
-    torch.cuda.synchronize()
-    steps = max(1, args.steps)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    g.gqt_profile_start()
-    ev[0].record()
-    for _ in range(steps):
-        g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
-    ev[1].record()
-    for _ in range(steps):
-        g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
-    ev[2].record()
-    torch.cuda.synchronize()
-    prof_ms, prof_n = g.gqt_profile_stop(10)
-    t_mom = ev[0].elapsed_time(ev[1]) * 1e-3 / steps
-    t_kb = ev[1].elapsed_time(ev[2]) * 1e-3 / steps
     n = lat.n
-    gemm_s = prof_ms[8] * 1e-3 / max(int(prof_n[8]), 1)
-    fma = 4.0 * M * M * n
     fp64_peak = g.gqt_probe_fp64()
-    s_np = sig.cpu().numpy()
-    e_np = E.cpu().numpy()
-    i0 = int(np.argmin(np.abs(e_np)))
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        bf16 = float(json.load(f)["bf16_tflops"])
+    tf32_peak = bf16 * 1.1 / 2.25  # nominal dense TF32 : BF16 ratio of the part
+    steps = max(1, args.steps)
     out = {"workload": f"haldane{L}x{L}_W1_M{M}", "n_orbitals": n, "moments": M, "vectors": 1,
            "metric": "Kubo-Bastin orbital-moment pairs/s (N R M^2 / time of gqt_kb_moments)",
-           "value": n * M * M / t_mom, "kb_moments_s": t_mom, "kubo_bastin_s": t_kb, "energies": int(E.numel()),
-           "kernels": {"k_kb_step_ms_per_launch": prof_ms[7] / max(int(prof_n[7]), 1), "k_kb_step_launches": int(prof_n[7]) // steps,
-                       "k_kb_gemm_ms": gemm_s * 1e3, "k_kb_integrand_ms": prof_ms[9] / max(int(prof_n[9]), 1)},
-           "roofline": {"kernel": "k_kb_gemm (M x M complex FP64 contraction over N)", "bound": "alu",
-                        "achieved": 2 * fma / gemm_s / 1e9, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                        "frac": 2 * fma / gemm_s / 1e9 / fp64_peak, "fp64_fma": fma,
-                        "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)"},
-           "sigma_xy_gap_centre_e2_over_h": float(s_np[i0]), "sigma_xy_energy": float(e_np[i0])}
+           "energies": int(E.numel()), "modes": {}}
+    sigmas = {}
+    for mode, name in ((1, "tensor_core_split_tf32"), (0, "fp64")):
+        if mode == 0 and args.hall_skip_fp64:
+            continue
+        g.gqt_set_kb_contraction(ham, mode)
+        lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+        sig = torch.empty_like(E)
+        for _ in range(max(1, args.warmup)):
+            g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+            g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        g.gqt_profile_start()
+        ev[0].record()
+        for _ in range(steps):
+            g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+        ev[1].record()
+        for _ in range(steps):
+            g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
+        ev[2].record()
+        torch.cuda.synchronize()
+        prof_ms, prof_n = g.gqt_profile_stop(10)
+        t_mom = ev[0].elapsed_time(ev[1]) * 1e-3 / steps
+        t_kb = ev[1].elapsed_time(ev[2]) * 1e-3 / steps
+        gemm_s = prof_ms[8] * 1e-3 / max(int(prof_n[8]), 1)
+        if mode == 0:
+            fma = 4.0 * M * M * n
+            roof = {"kernel": "k_kb_gemm (complex FP64 contraction)", "bound": "alu", "achieved": 2 * fma / gemm_s / 1e9,
+                    "peak": fp64_peak, "unit": "GFLOP/s (FP64)", "frac": 2 * fma / gemm_s / 1e9 / fp64_peak,
+                    "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)"}
+        else:
+            macs = 3.0 * 2 * M * M * (2.0 * n)  # three split products, Re and Im, 2N real terms
+            roof = {"kernel": "k_kb_gemm_tc (tcgen05 kind::tf32, three split products)", "bound": "tensor",
+                    "achieved": 2 * macs / gemm_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s (TF32)",
+                    "frac": 2 * macs / gemm_s / 1e12 / tf32_peak,
+                    "peak_source": "measured BF16 GEMM (MEASURED_PEAKS.json bf16_tflops) x nominal TF32/BF16 1.1/2.25"}
+        s_np = sig.cpu().numpy()
+        sigmas[mode] = s_np
+        e_np = E.cpu().numpy()
+        i0 = int(np.argmin(np.abs(e_np)))
+        out["modes"][name] = {
+            "value": n * M * M / t_mom, "kb_moments_s": t_mom, "kubo_bastin_s": t_kb,
+            "kernels": {"k_kb_step_ms_per_launch": prof_ms[7] / max(int(prof_n[7]), 1),
+                        "k_kb_step_launches": int(prof_n[7]) // steps, "contraction_ms": gemm_s * 1e3,
+                        "k_kb_integrand_ms": prof_ms[9] / max(int(prof_n[9]), 1)},
+            "roofline": roof, "sigma_xy_gap_centre_e2_over_h": float(s_np[i0])}
+    if 0 in sigmas and 1 in sigmas:
+        out["sigma_xy_max_abs_diff_tc_vs_fp64"] = float(np.max(np.abs(sigmas[1] - sigmas[0])))
+    first = out["modes"].get("tensor_core_split_tf32") or out["modes"]["fp64"]
+    out["value"] = first["value"]
     if not args.no_cpu_baseline:
         import oracle as O  # the CPU baseline leg only
         h = O.Hamiltonian(lat, dE)
@@ -715,6 +738,7 @@ def main():
     ap.add_argument("--hall", action="store_true", help="Hall conductivity (Kubo-Bastin) of the Haldane model")
     ap.add_argument("--hall-L", type=int, default=0, help="Haldane cells per side of the Hall run (profiling)")
     ap.add_argument("--hall-moments", type=int, default=0, help="Kubo-Bastin moments of the Hall run (profiling)")
+    ap.add_argument("--hall-skip-fp64", action="store_true", help="time only the tensor-core contraction (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

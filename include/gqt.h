@@ -222,6 +222,14 @@ gqt_status gqt_bond_gradients(const double* d_g_slot, long long n_slots, const l
 gqt_status gqt_kb_moments(gqt_ham* ham, const void* d_r, int R, int M, int alpha, int beta, double* d_lambda,
                           void* stream);
 
+/* How gqt_kb_moments contracts the two stacks (default 0):
+ * 0 = FP64 (complex FP64 GEMM on the FP64 pipe; Lambda to FP64 rounding);
+ * 1 = split TF32 on the tcgen05 tensor cores: both stacks are rounded to pairs of
+ *     TF32 numbers (hi + lo, about 22 bits), each product is hi*hi + hi*lo + lo*hi,
+ *     accumulated in FP32 over splits of about 16K terms and summed in FP64
+ *     (Lambda to about 1e-6 of its largest entries).  The chains stay FP64. */
+gqt_status gqt_set_kb_contraction(gqt_ham* ham, int mode);
+
 /* sigma_ab(E_j) in units of e^2/h at zero temperature from Kubo-Bastin moments:
  *   sigma(E_j) = (2/area) int_{x_0}^{x_j} dx F(x),  x = E/dE = cos th,
  *   F(x) = (1 - x^2)^-2 Re sum_mn c_m c_n g_m g_n Gamma_mn(x) Lambda_mn,

@@ -57,6 +57,7 @@ _SIGS = {
     "gqt_kpm_reconstruct": [_P, _I, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kpm_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _P],
     "gqt_kb_moments": [_P, _P, _I, _I, _I, _I, _P, _P],
+    "gqt_set_kb_contraction": [_P, _I],
     "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
     "gqt_bond_gradients": [_P, _I64, _P, _P, _I, _P, _P, _P],
@@ -326,6 +327,11 @@ def gqt_kb_moments(ham: Ham, r, R: int, M: int, alpha: int, beta: int, lam, stre
     _check(lib().gqt_kb_moments(ham.ptr, _dptr(r, "r"), int(R), int(M), int(alpha), int(beta), _dptr(lam, "lam"),
                                 _stream(stream)))
     return lam
+
+
+def gqt_set_kb_contraction(ham: Ham, mode: int):
+    """0 = FP64 contraction of the Hall moments (default), 1 = split TF32 on the tensor cores."""
+    _check(lib().gqt_set_kb_contraction(ham.ptr, int(mode)))
 
 
 def gqt_kubo_bastin(lam, E, energy_scale: float, area: float, sigma, kernel: int = 0, stream=None):

@@ -65,10 +65,29 @@ __device__ __forceinline__ double2 mla(double2 acc, double2 h, double2 x) {
   return acc;
 }
 
-// y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2).
+// Split of an FP64 value into two TF32 numbers (FP32 with the low 13 mantissa
+// bits zero, as the tensor cores read them): hi = x rounded to TF32, lo = x - hi
+// rounded to FP32 (the tensor cores keep its top 11 bits).  hi + lo carries about
+// 22 significant bits.
+__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+  const float f = (float)x;
+  hi = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
+  lo = (float)(x - (double)hi);
+}
+__device__ __forceinline__ void store_split(float2* hi, float2* lo, size_t e, double2 v) {
+  float2 h, l;
+  split_tf32(v.x, h.x, l.x);
+  split_tf32(v.y, h.y, l.y);
+  hi[e] = h;
+  lo[e] = l;
+}
+
+// y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2); with
+// yhi/ylo also its TF32 split (the tensor-core contraction's operands).
 template <bool CH>
 __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R, size_t total,
-                              const double2* __restrict__ x, double2* __restrict__ y) {
+                              const double2* __restrict__ x, double2* __restrict__ y, float2* __restrict__ yhi,
+                              float2* __restrict__ ylo) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
@@ -78,7 +97,9 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
       const double2 xj = x[(size_t)H.idx[sl] * R + r];
       s = mla(s, H.hop2[sl], make_double2(d[sl] * xj.x, d[sl] * xj.y));
     }
-    y[e] = make_double2(-0.5 * s.y, 0.5 * s.x);
+    const double2 v = make_double2(-0.5 * s.y, 0.5 * s.x);
+    y[e] = v;
+    if (yhi) store_split(yhi, ylo, e, v);
   }
 }
 
@@ -86,12 +107,16 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
 //   P_{k+1} = 2H~P_k - P_{k-1}   (P_1 = H~P_0 at k = 0), unless last
 //   Q_{k+1} = 2H~Q_k - Q_{k-1}   (Q_1 = H~Q_0),           unless last
 //   B_k = v~_b Q_k                (from the same gathers of Q_k)
+// TC: P_{k+1} and B_k also (or, for B_k, only) go to the TF32-split stacks
+// (phi/plo entry k+1, bhi/blo entry k); bout may then be null.
 template <bool CH>
 __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __restrict__ db, int R, size_t total,
                                                  const double2* __restrict__ pk, const double2* __restrict__ pkm1,
                                                  double2* __restrict__ pout, const double2* __restrict__ qk,
                                                  const double2* __restrict__ qkm1, double2* __restrict__ qout,
-                                                 double2* __restrict__ bout, int first, int last) {
+                                                 double2* __restrict__ bout, int first, int last,
+                                                 float2* __restrict__ phi, float2* __restrict__ plo,
+                                                 float2* __restrict__ bhi, float2* __restrict__ blo) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
@@ -106,18 +131,23 @@ __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __
       b = mla(b, h2, make_double2(db[sl] * qj.x, db[sl] * qj.y));
       if (!last) a = mla(a, h2, pk[j]);
     }
-    bout[e] = make_double2(-0.5 * b.y, 0.5 * b.x);
+    const double2 bv = make_double2(-0.5 * b.y, 0.5 * b.x);
+    if (bout) bout[e] = bv;
+    if (bhi) store_split(bhi, blo, e, bv);
     if (last) continue;
     a = mla(a, dg, pk[e]);
     q = mla(q, dg, qk[e]);
+    double2 pn;
     if (first) {
-      pout[e] = make_double2(0.5 * a.x, 0.5 * a.y);
+      pn = make_double2(0.5 * a.x, 0.5 * a.y);
       qout[e] = make_double2(0.5 * q.x, 0.5 * q.y);
     } else {
       const double2 p0 = pkm1[e], q0 = qkm1[e];
-      pout[e] = make_double2(a.x - p0.x, a.y - p0.y);
+      pn = make_double2(a.x - p0.x, a.y - p0.y);
       qout[e] = make_double2(q.x - q0.x, q.y - q0.y);
     }
+    pout[e] = pn;
+    if (phi) store_split(phi, plo, e, pn);
   }
 }
 
@@ -178,6 +208,176 @@ __global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ 
       const int m = m0 + tm + 16 * u, nn = n0 + tn + 16 * v;
       if (m < M && nn < M) part[((size_t)blockIdx.z * M + m) * M + nn] = acc[u][v];
     }
+}
+
+// ------------------------------------------------------------ tensor-core contraction
+// The same contraction on the tcgen05 tensor cores in split TF32 (three products
+// hi*hi + hi*lo + lo*hi per pair, FP32 accumulation in tensor memory over one
+// split of the contraction, splits summed in FP64).  Complex to real: with the
+// stacks stored as interleaved (re, im) floats, Re Lambda_mn = sum P_m . B_n
+// over the floats, and Im Lambda_mn = sum P_m . B'_n with B' = (im, -re) per
+// complex element, built in shared memory from the B tile.  One CTA of 128
+// threads computes a 128 x 128 tile of Re and of Im (two accumulators of 128
+// TMEM columns each), two shared-memory stages of 32 floats along the
+// contraction, operands K-major without swizzle: core matrices of 8 rows x 16 B,
+// K-adjacent ones TC_LBO bytes apart (144, so the 8 chunks of one row land in
+// distinct banks), 8-row groups TC_SBO bytes apart.
+constexpr int TC_TM = 128, TC_TK = 32, TC_LBO = 144, TC_SBO = 8 * TC_LBO, TC_TILE = 16 * TC_SBO;
+constexpr int TC_STAGE = 6 * TC_TILE;  // P hi/lo, B hi/lo, B' hi/lo
+constexpr int TC_SMEM = 2 * TC_STAGE + 64;
+constexpr int TC_WAIT_LIMIT = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  // kind::tf32, D f32, A and B K-major, M = 128, N = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity));
+  return done != 0;
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// 16 bytes of a K-major stack row: floats k..k+3 of row `row` (zeros past M or Kr).
+__device__ __forceinline__ float4 tc_load(const float* __restrict__ src, int row, int M, size_t Kr, size_t k,
+                                          size_t ke) {
+  if (row >= M || k >= ke) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* p = src + (size_t)row * Kr + k;
+  if (k + 4 <= ke && ((Kr & 3) == 0)) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v;
+  v.x = p[0];
+  v.y = k + 1 < ke ? p[1] : 0.f;
+  v.z = k + 2 < ke ? p[2] : 0.f;
+  v.w = k + 3 < ke ? p[3] : 0.f;
+  return v;
+}
+
+__global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(const float* __restrict__ Phi, const float* __restrict__ Plo,
+                                                       const float* __restrict__ Bhi, const float* __restrict__ Blo,
+                                                       int M, size_t Kr, size_t kchunk, double2* __restrict__ part,
+                                                       int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tc_sm + 2 * TC_STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_sm + 2 * TC_STAGE + 32);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * TC_TM, n0 = blockIdx.y * TC_TM;
+  const size_t kb = (size_t)blockIdx.z * kchunk;
+  const size_t ke = (kb + kchunk < Kr) ? kb + kchunk : Kr;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const int nst = (int)((ke - kb + TC_TK - 1) / TC_TK);
+  bool ok = true;
+  for (int s = 0; s < nst; ++s) {
+    const int buf = s & 1;
+    unsigned char* st = tc_sm + buf * TC_STAGE;
+    // the products of stage s - 2 read this buffer: wait for them (block-uniform
+    // outcome, so that every thread takes the same path through the barriers)
+    if (s >= 2 && !__syncthreads_and(tc_wait(&bar[buf], (uint32_t)(((s - 2) >> 1) & 1)))) {
+      ok = false;
+      break;
+    }
+    // fill: 8 passes of 16 rows; thread -> (row, 16-byte chunk kq), the 8 chunks of
+    // a row read by 8 consecutive threads (128 contiguous bytes)
+    const size_t k0 = kb + (size_t)s * TC_TK;
+#pragma unroll 2
+    for (int pss = 0; pss < 8; ++pss) {
+      const int row = pss * 16 + (tid >> 3), kq = tid & 7;
+      const size_t k = k0 + 4 * kq;
+      const int off = (row >> 3) * TC_SBO + kq * TC_LBO + (row & 7) * 16;
+      const float4 ph = tc_load(Phi, m0 + row, M, Kr, k, ke), pl = tc_load(Plo, m0 + row, M, Kr, k, ke);
+      const float4 bh = tc_load(Bhi, n0 + row, M, Kr, k, ke), bl = tc_load(Blo, n0 + row, M, Kr, k, ke);
+      *reinterpret_cast<float4*>(st + 0 * TC_TILE + off) = ph;
+      *reinterpret_cast<float4*>(st + 1 * TC_TILE + off) = pl;
+      *reinterpret_cast<float4*>(st + 2 * TC_TILE + off) = bh;
+      *reinterpret_cast<float4*>(st + 3 * TC_TILE + off) = bl;
+      *reinterpret_cast<float4*>(st + 4 * TC_TILE + off) = make_float4(bh.y, -bh.x, bh.w, -bh.z);
+      *reinterpret_cast<float4*>(st + 5 * TC_TILE + off) = make_float4(bl.y, -bl.x, bl.w, -bl.z);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t base = smem_addr(st);
+#pragma unroll
+      for (int j = 0; j < TC_TK / 8; ++j) {
+        const uint32_t o = (uint32_t)(j * 2 * TC_LBO);
+        const uint64_t ah = tc_desc(base + 0 * TC_TILE + o), al = tc_desc(base + 1 * TC_TILE + o);
+        const uint64_t bh = tc_desc(base + 2 * TC_TILE + o), bl = tc_desc(base + 3 * TC_TILE + o);
+        const uint64_t qh = tc_desc(base + 4 * TC_TILE + o), ql = tc_desc(base + 5 * TC_TILE + o);
+        const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+        tc_mma(tmem, ah, bh, acc);
+        tc_mma(tmem, ah, bl, 1u);
+        tc_mma(tmem, al, bh, 1u);
+        tc_mma(tmem + 128, ah, qh, acc);
+        tc_mma(tmem + 128, ah, ql, 1u);
+        tc_mma(tmem + 128, al, qh, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(&bar[buf])));
+    }
+  }
+  // the last stage's products (or, after a timeout, whatever is still in flight)
+  ok = __syncthreads_and(ok && (nst == 0 || tc_wait(&bar[(nst - 1) & 1], (uint32_t)(((nst - 1) >> 1) & 1))));
+  if (!ok && tid == 0) atomicOr(err, 16);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int m = m0 + warp * 32 + (tid & 31);
+    for (int c = 0; c < TC_TM; c += 32) {
+      uint32_t re[32], im[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, re);
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128 + c, im);
+      if (m < M) {
+        double2* dst = part + ((size_t)blockIdx.z * M + m) * M + n0 + c;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (n0 + c + j < M) dst[j] = make_double2((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
 // lam[m][n] = scale * sum_s part[s][m][n], splits summed in order (deterministic).
@@ -300,43 +500,92 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   H.idx = (const int*)h->d_idx.p;
   H.hop2 = (const typename HallEll<CH>::HT*)h->d_hop.p;
   H.diag2 = (const double*)h->d_diag.p;
+  const bool tc = h->kb_mode == 1;
   const size_t total = (size_t)h->n * R;
-  const size_t vb = total * sizeof(double2);
-  double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
-  double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
-  double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
+  const size_t vb = total * sizeof(double2), fb = total * sizeof(float2);
   const int g = grid_for(total);
-  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst);
-  check_launch("k_kb_velocity");
+  double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
   auto qbuf = [&](int k) -> double2* { return Q + (size_t)(k % 3) * total; };
+  const size_t mm = (size_t)M * M;
+  if (!tc) {
+    double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
+    double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
+    k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, nullptr, nullptr);
+    check_launch("k_kb_velocity");
+    for (int k = 0; k < M; ++k) {
+      const bool last = k == M - 1;
+      const double2* qk = k == 0 ? r : qbuf(k);
+      const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
+      const size_t pe = prof_begin(st);
+      k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
+                                        k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
+                                        last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
+                                        last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last, nullptr,
+                                        nullptr, nullptr, nullptr);
+      check_launch("k_kb_step");
+      prof_end(pe, 7, st);
+    }
+    // split of the contraction: about eight waves of two resident CTAs per SM, at
+    // least 512 contraction elements per split
+    const int tiles = (M + KB_TM - 1) / KB_TM;
+    const long long slots = 2LL * gqt::sm_count();
+    long long S = std::max<long long>(1, (8 * slots + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
+    S = std::min<long long>(S, std::max<long long>(1, (long long)(total / 512)));
+    const size_t kchunk = ((total + S - 1) / S + KB_TK - 1) / KB_TK * KB_TK;
+    S = (long long)((total + kchunk - 1) / kchunk);
+    double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * mm * sizeof(double2)).p;
+    const size_t pg = prof_begin(st);
+    k_kb_gemm<<<dim3(tiles, tiles, (unsigned)S), 256, 0, st>>>(Pst, Bst, M, total, kchunk, part);
+    check_launch("k_kb_gemm");
+    prof_end(pg, 8, st);
+    k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M,
+                                                                                (double)h->n / R, lam);
+    check_launch("k_kb_reduce");
+    return;
+  }
+  // tensor-core contraction: chains in FP64 (rolling buffers), stacks in split TF32
+  double2* Pr = (double2*)h->ws(WS_HALL_P, vb * 3).p;
+  auto pbuf = [&](int k) -> double2* { return Pr + (size_t)(k % 3) * total; };
+  float2* Phi = (float2*)h->ws(WS_HALL_B, fb * M * 4).p;
+  float2* Plo = Phi + (size_t)M * total;
+  float2* Bhi = Plo + (size_t)M * total;
+  float2* Blo = Bhi + (size_t)M * total;
+  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), Phi, Plo);
+  check_launch("k_kb_velocity");
   for (int k = 0; k < M; ++k) {
     const bool last = k == M - 1;
     const double2* qk = k == 0 ? r : qbuf(k);
     const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
     const size_t pe = prof_begin(st);
-    k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
-                                      k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
-                                      last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
-                                      last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last);
+    k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
+                                      last ? nullptr : pbuf(k + 1), qk, qkm1, last ? nullptr : qbuf(k + 1), nullptr,
+                                      k == 0, last, last ? nullptr : Phi + (size_t)(k + 1) * total,
+                                      last ? nullptr : Plo + (size_t)(k + 1) * total, Bhi + (size_t)k * total,
+                                      Blo + (size_t)k * total);
     check_launch("k_kb_step");
     prof_end(pe, 7, st);
   }
-  // split of the contraction: about eight waves of two resident CTAs per SM, at
-  // least 512 contraction elements per split
-  const int tiles = (M + KB_TM - 1) / KB_TM;
-  const long long slots = 2LL * gqt::sm_count();
-  long long S = std::max<long long>(1, (8 * slots + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
-  S = std::min<long long>(S, std::max<long long>(1, (long long)(total / 512)));
-  const size_t kchunk = ((total + S - 1) / S + KB_TK - 1) / KB_TK * KB_TK;
-  S = (long long)((total + kchunk - 1) / kchunk);
-  double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * M * M * sizeof(double2)).p;
+  // splits: contraction chunks of about 16K floats (the FP32 accumulation span)
+  // and at least four waves of one CTA per SM
+  const size_t Kr = 2 * total;
+  const int tiles = (M + TC_TM - 1) / TC_TM;
+  long long S = std::max<long long>((long long)((Kr + 16383) / 16384),
+                                    (4LL * gqt::sm_count() + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
+  S = std::min<long long>(S, std::max<long long>(1, (long long)(Kr / TC_TK)));
+  const size_t kchunk = ((Kr + S - 1) / S + TC_TK - 1) / TC_TK * TC_TK;
+  S = (long long)((Kr + kchunk - 1) / kchunk);
+  double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * mm * sizeof(double2)).p;
+  check_cuda(cudaFuncSetAttribute(k_kb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM),
+             "smem attribute");
+  check_cuda(cudaMemsetAsync(h->d_flag.p, 0, sizeof(int), st), "flag reset");
   const size_t pg = prof_begin(st);
-  k_kb_gemm<<<dim3(tiles, tiles, (unsigned)S), 256, 0, st>>>(Pst, Bst, M, total, kchunk, part);
-  check_launch("k_kb_gemm");
+  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), 128, TC_SMEM, st>>>((const float*)Phi, (const float*)Plo,
+                                                                      (const float*)Bhi, (const float*)Blo, M, Kr,
+                                                                      kchunk, part, (int*)h->d_flag.p);
+  check_launch("k_kb_gemm_tc");
   prof_end(pg, 8, st);
-  const size_t mm = (size_t)M * M;
-  k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M,
-                                                                              (double)h->n / R, lam);
+  k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M, (double)h->n / R,
+                                                                              lam);
   check_launch("k_kb_reduce");
 }
 
@@ -358,7 +607,11 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
       kb_moments_impl<false>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
     else
       kb_moments_impl<true>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
+    int flag = 0;
+    if (h->kb_mode == 1)
+      check_cuda(cudaMemcpyAsync(&flag, h->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     check_cuda(cudaStreamSynchronize(st), "gqt_kb_moments");
+    if (flag & 16) throw Error(GQT_ETIMEOUT, "gqt_kb_moments: a bounded tensor-core wait gave up");
     return GQT_OK;
   } catch (const Error& e) {
     set_error(e.what());
@@ -370,6 +623,15 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
     set_error(std::string("internal error: ") + e.what());
     return GQT_ECUDA;
   }
+}
+
+extern "C" gqt_status gqt_set_kb_contraction(gqt_ham* h, int mode) {
+  if (!h || mode < 0 || mode > 1) {
+    set_error("gqt_set_kb_contraction: bad argument");
+    return GQT_EINVAL;
+  }
+  h->kb_mode = mode;
+  return GQT_OK;
 }
 
 extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,

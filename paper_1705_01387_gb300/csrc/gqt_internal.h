@@ -92,6 +92,7 @@ struct gqt_ham {
   bool use_graphs = true;
   bool use_cluster = true;  // cluster-resident moment rows for small systems
   bool use_pair = true;     // l != r moment rows by two recurrences (two moments per step)
+  int kb_mode = 0;          // Hall moment contraction: 0 FP64, 1 split TF32 on the tensor cores
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;
