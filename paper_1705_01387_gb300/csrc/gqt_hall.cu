@@ -74,20 +74,25 @@ __device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
   hi = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
   lo = (float)(x - (double)hi);
 }
-__device__ __forceinline__ void store_split(float2* hi, float2* lo, size_t e, double2 v) {
-  float2 h, l;
-  split_tf32(v.x, h.x, l.x);
-  split_tf32(v.y, h.y, l.y);
-  hi[e] = h;
-  lo[e] = l;
+// Planar TF32-split stack entry: re_hi, im_hi, re_lo, im_lo planes (null re_hi: none).
+struct TcPlanes {
+  float *re_hi, *im_hi, *re_lo, *im_lo;
+};
+__device__ __forceinline__ void store_split(const TcPlanes& t, size_t e, double2 v) {
+  float h, l;
+  split_tf32(v.x, h, l);
+  t.re_hi[e] = h;
+  t.re_lo[e] = l;
+  split_tf32(v.y, h, l);
+  t.im_hi[e] = h;
+  t.im_lo[e] = l;
 }
 
 // y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2); with
 // yhi/ylo also its TF32 split (the tensor-core contraction's operands).
 template <bool CH>
 __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R, size_t total,
-                              const double2* __restrict__ x, double2* __restrict__ y, float2* __restrict__ yhi,
-                              float2* __restrict__ ylo) {
+                              const double2* __restrict__ x, double2* __restrict__ y, TcPlanes ys) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
@@ -99,7 +104,7 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
     }
     const double2 v = make_double2(-0.5 * s.y, 0.5 * s.x);
     y[e] = v;
-    if (yhi) store_split(yhi, ylo, e, v);
+    if (ys.re_hi) store_split(ys, e, v);
   }
 }
 
@@ -107,16 +112,15 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
 //   P_{k+1} = 2H~P_k - P_{k-1}   (P_1 = H~P_0 at k = 0), unless last
 //   Q_{k+1} = 2H~Q_k - Q_{k-1}   (Q_1 = H~Q_0),           unless last
 //   B_k = v~_b Q_k                (from the same gathers of Q_k)
-// TC: P_{k+1} and B_k also (or, for B_k, only) go to the TF32-split stacks
-// (phi/plo entry k+1, bhi/blo entry k); bout may then be null.
+// TC: P_{k+1} and B_k also (or, for B_k, only) go to the planar TF32-split stacks
+// (ps: entry k+1, bs: entry k); bout may then be null.
 template <bool CH>
 __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __restrict__ db, int R, size_t total,
                                                  const double2* __restrict__ pk, const double2* __restrict__ pkm1,
                                                  double2* __restrict__ pout, const double2* __restrict__ qk,
                                                  const double2* __restrict__ qkm1, double2* __restrict__ qout,
-                                                 double2* __restrict__ bout, int first, int last,
-                                                 float2* __restrict__ phi, float2* __restrict__ plo,
-                                                 float2* __restrict__ bhi, float2* __restrict__ blo) {
+                                                 double2* __restrict__ bout, int first, int last, TcPlanes ps,
+                                                 TcPlanes bs) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __
     }
     const double2 bv = make_double2(-0.5 * b.y, 0.5 * b.x);
     if (bout) bout[e] = bv;
-    if (bhi) store_split(bhi, blo, e, bv);
+    if (bs.re_hi) store_split(bs, e, bv);
     if (last) continue;
     a = mla(a, dg, pk[e]);
     q = mla(q, dg, qk[e]);
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __
       qout[e] = make_double2(q.x - q0.x, q.y - q0.y);
     }
     pout[e] = pn;
-    if (phi) store_split(phi, plo, e, pn);
+    if (ps.re_hi) store_split(ps, e, pn);
   }
 }
 
@@ -213,19 +217,26 @@ __global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ 
 // ------------------------------------------------------------ tensor-core contraction
 // The same contraction on the tcgen05 tensor cores in split TF32 (three products
 // hi*hi + hi*lo + lo*hi per pair, FP32 accumulation in tensor memory over one
-// split of the contraction, splits summed in FP64).  Complex to real: with the
-// stacks stored as interleaved (re, im) floats, Re Lambda_mn = sum P_m . B_n
-// over the floats, and Im Lambda_mn = sum P_m . B'_n with B' = (im, -re) per
-// complex element, built in shared memory from the B tile.  One CTA of 128
-// threads computes a 128 x 128 tile of Re and of Im (two accumulators of 128
-// TMEM columns each), two shared-memory stages of 32 floats along the
-// contraction, operands K-major without swizzle: core matrices of 8 rows x 16 B,
-// K-adjacent ones TC_LBO bytes apart (144, so the 8 chunks of one row land in
-// distinct banks), 8-row groups TC_SBO bytes apart.
-constexpr int TC_TM = 128, TC_TK = 32, TC_LBO = 144, TC_SBO = 8 * TC_LBO, TC_TILE = 16 * TC_SBO;
-constexpr int TC_STAGE = 6 * TC_TILE;  // P hi/lo, B hi/lo, B' hi/lo
-constexpr int TC_SMEM = 2 * TC_STAGE + 64;
+// split of the contraction, splits summed in FP64).  The stacks are planar
+// (real and imaginary planes [M][ld], ld = N R rounded up to 4), so with
+//   Re Lambda = Pre.Bre + Pim.Bim,  Im Lambda = Pre.Bim - Pim.Bre
+// every operand is a plain tile of a plane.  One CTA of 128 threads computes a
+// 128 x 128 output tile into three accumulators of 128 tensor-memory columns
+// (Re, Pre.Bim, Pim.Bre); contraction stages of 16 sites pass through three
+// shared-memory buffers filled by cp.async two stages ahead of the products.
+// Operands are K-major without swizzle: core matrices of 8 rows x 16 B,
+// K-adjacent ones TC_LBO bytes apart (144, so a row's chunks land in distinct
+// banks), 8-row groups TC_SBO bytes apart.
+constexpr int TC_TM = 128, TC_TK = 16, TC_LBO = 144, TC_SBO = 4 * TC_LBO, TC_TILE = 16 * TC_SBO;
+constexpr int TC_NT = 8;                      // Pre hi/lo, Pim hi/lo, Bre hi/lo, Bim hi/lo
+constexpr int TC_STAGE = TC_NT * TC_TILE;     // 73,728 B
+constexpr int TC_NBUF = 3;
+constexpr int TC_SMEM = TC_NBUF * TC_STAGE + 64;
 constexpr int TC_WAIT_LIMIT = 1 << 24;
+
+struct TcOperands {
+  const float* plane[TC_NT];  // same order as the shared-memory tiles
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -266,39 +277,42 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// 16 bytes of a K-major stack row: floats k..k+3 of row `row` (zeros past M or Kr).
-__device__ __forceinline__ float4 tc_load(const float* __restrict__ src, int row, int M, size_t Kr, size_t k,
-                                          size_t ke) {
-  if (row >= M || k >= ke) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const float* p = src + (size_t)row * Kr + k;
-  if (k + 4 <= ke && ((Kr & 3) == 0)) return __ldg(reinterpret_cast<const float4*>(p));
-  float4 v;
-  v.x = p[0];
-  v.y = k + 1 < ke ? p[1] : 0.f;
-  v.z = k + 2 < ke ? p[2] : 0.f;
-  v.w = k + 3 < ke ? p[3] : 0.f;
-  return v;
+// One stage of copies: 8 tiles x 128 rows x 4 chunks of 16 B, four per thread
+// per tile; rows past M and sites past ke are filled with zeros (source size 0).
+__device__ __forceinline__ void tc_fill(const TcOperands& op, unsigned char* st, int m0, int n0, int M, size_t ld,
+                                        size_t k0, size_t ke) {
+#pragma unroll
+  for (int t = 0; t < TC_NT; ++t) {
+    const int base = t < 4 ? m0 : n0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + 128 * q;
+      const int row = idx >> 2, kq = idx & 3;
+      const size_t k = k0 + 4 * kq;
+      const bool valid = base + row < M && k < ke;
+      const float* src = valid ? op.plane[t] + (size_t)(base + row) * ld + k : op.plane[t];
+      const uint32_t dst = smem_addr(st + t * TC_TILE + (row >> 3) * TC_SBO + kq * TC_LBO + (row & 7) * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0));
+    }
+  }
 }
 
-__global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(const float* __restrict__ Phi, const float* __restrict__ Plo,
-                                                       const float* __restrict__ Bhi, const float* __restrict__ Blo,
-                                                       int M, size_t Kr, size_t kchunk, double2* __restrict__ part,
-                                                       int* __restrict__ err) {
+__global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(TcOperands op, int M, size_t ld, size_t kchunk,
+                                                       double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tc_sm + 2 * TC_STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_sm + 2 * TC_STAGE + 32);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tc_sm + TC_NBUF * TC_STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_sm + TC_NBUF * TC_STAGE + 32);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m0 = blockIdx.x * TC_TM, n0 = blockIdx.y * TC_TM;
   const size_t kb = (size_t)blockIdx.z * kchunk;
-  const size_t ke = (kb + kchunk < Kr) ? kb + kchunk : Kr;
+  const size_t ke = (kb + kchunk < ld) ? kb + kchunk : ld;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[1])), "r"(1));
+    for (int b = 0; b < TC_NBUF; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[b])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -306,78 +320,82 @@ __global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(const float* __restrict__
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
   const int nst = (int)((ke - kb + TC_TK - 1) / TC_TK);
+  // prologue: stages 0 and 1 in flight (a group is committed for every stage index,
+  // empty past the end, so that wait_group counts stay uniform)
+  for (int s = 0; s < 2; ++s) {
+    if (s < nst) tc_fill(op, tc_sm + s * TC_STAGE, m0, n0, M, ld, kb + (size_t)s * TC_TK, ke);
+    asm volatile("cp.async.commit_group;");
+  }
   bool ok = true;
   for (int s = 0; s < nst; ++s) {
-    const int buf = s & 1;
-    unsigned char* st = tc_sm + buf * TC_STAGE;
-    // the products of stage s - 2 read this buffer: wait for them (block-uniform
-    // outcome, so that every thread takes the same path through the barriers)
-    if (s >= 2 && !__syncthreads_and(tc_wait(&bar[buf], (uint32_t)(((s - 2) >> 1) & 1)))) {
-      ok = false;
-      break;
-    }
-    // fill: 8 passes of 16 rows; thread -> (row, 16-byte chunk kq), the 8 chunks of
-    // a row read by 8 consecutive threads (128 contiguous bytes)
-    const size_t k0 = kb + (size_t)s * TC_TK;
-#pragma unroll 2
-    for (int pss = 0; pss < 8; ++pss) {
-      const int row = pss * 16 + (tid >> 3), kq = tid & 7;
-      const size_t k = k0 + 4 * kq;
-      const int off = (row >> 3) * TC_SBO + kq * TC_LBO + (row & 7) * 16;
-      const float4 ph = tc_load(Phi, m0 + row, M, Kr, k, ke), pl = tc_load(Plo, m0 + row, M, Kr, k, ke);
-      const float4 bh = tc_load(Bhi, n0 + row, M, Kr, k, ke), bl = tc_load(Blo, n0 + row, M, Kr, k, ke);
-      *reinterpret_cast<float4*>(st + 0 * TC_TILE + off) = ph;
-      *reinterpret_cast<float4*>(st + 1 * TC_TILE + off) = pl;
-      *reinterpret_cast<float4*>(st + 2 * TC_TILE + off) = bh;
-      *reinterpret_cast<float4*>(st + 3 * TC_TILE + off) = bl;
-      *reinterpret_cast<float4*>(st + 4 * TC_TILE + off) = make_float4(bh.y, -bh.x, bh.w, -bh.z);
-      *reinterpret_cast<float4*>(st + 5 * TC_TILE + off) = make_float4(bl.y, -bl.x, bl.w, -bl.z);
-    }
+    const int buf = s % TC_NBUF;
+    asm volatile("cp.async.wait_group 1;");
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
-      const uint32_t base = smem_addr(st);
+      const uint32_t base = smem_addr(tc_sm + buf * TC_STAGE);
 #pragma unroll
       for (int j = 0; j < TC_TK / 8; ++j) {
         const uint32_t o = (uint32_t)(j * 2 * TC_LBO);
-        const uint64_t ah = tc_desc(base + 0 * TC_TILE + o), al = tc_desc(base + 1 * TC_TILE + o);
-        const uint64_t bh = tc_desc(base + 2 * TC_TILE + o), bl = tc_desc(base + 3 * TC_TILE + o);
-        const uint64_t qh = tc_desc(base + 4 * TC_TILE + o), ql = tc_desc(base + 5 * TC_TILE + o);
+        uint64_t d[TC_NT];
+#pragma unroll
+        for (int t = 0; t < TC_NT; ++t) d[t] = tc_desc(base + t * TC_TILE + o);
+        // d: 0 Pre_hi, 1 Pre_lo, 2 Pim_hi, 3 Pim_lo, 4 Bre_hi, 5 Bre_lo, 6 Bim_hi, 7 Bim_lo
         const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
-        tc_mma(tmem, ah, bh, acc);
-        tc_mma(tmem, ah, bl, 1u);
-        tc_mma(tmem, al, bh, 1u);
-        tc_mma(tmem + 128, ah, qh, acc);
-        tc_mma(tmem + 128, ah, ql, 1u);
-        tc_mma(tmem + 128, al, qh, 1u);
+        tc_mma(tmem, d[0], d[4], acc);
+        tc_mma(tmem, d[0], d[5], 1u);
+        tc_mma(tmem, d[1], d[4], 1u);
+        tc_mma(tmem, d[2], d[6], 1u);
+        tc_mma(tmem, d[2], d[7], 1u);
+        tc_mma(tmem, d[3], d[6], 1u);
+        tc_mma(tmem + 128, d[0], d[6], acc);
+        tc_mma(tmem + 128, d[0], d[7], 1u);
+        tc_mma(tmem + 128, d[1], d[6], 1u);
+        tc_mma(tmem + 256, d[2], d[4], acc);
+        tc_mma(tmem + 256, d[2], d[5], 1u);
+        tc_mma(tmem + 256, d[3], d[4], 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_addr(&bar[buf])));
     }
+    // stage s + 2 reuses the buffer of stage s - 1: wait for its products
+    // (block-uniform outcome, so every thread takes the same path)
+    if (s >= 1 && !__syncthreads_and(tc_wait(&bar[(s - 1) % TC_NBUF], (uint32_t)(((s - 1) / TC_NBUF) & 1)))) {
+      ok = false;
+      break;
+    }
+    if (s + 2 < nst)
+      tc_fill(op, tc_sm + ((s + 2) % TC_NBUF) * TC_STAGE, m0, n0, M, ld, kb + (size_t)(s + 2) * TC_TK, ke);
+    asm volatile("cp.async.commit_group;");
   }
+  asm volatile("cp.async.wait_all;");
   // the last stage's products (or, after a timeout, whatever is still in flight)
-  ok = __syncthreads_and(ok && (nst == 0 || tc_wait(&bar[(nst - 1) & 1], (uint32_t)(((nst - 1) >> 1) & 1))));
+  ok = __syncthreads_and(ok && (nst == 0 || tc_wait(&bar[(nst - 1) % TC_NBUF], (uint32_t)(((nst - 1) / TC_NBUF) & 1))));
   if (!ok && tid == 0) atomicOr(err, 16);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     const int m = m0 + warp * 32 + (tid & 31);
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
     for (int c = 0; c < TC_TM; c += 32) {
-      uint32_t re[32], im[32];
-      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, re);
-      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128 + c, im);
+      uint32_t re[32], ia[32], ib[32];
+      tc_ld32(tmem + lane + c, re);
+      tc_ld32(tmem + lane + 128 + c, ia);
+      tc_ld32(tmem + lane + 256 + c, ib);
       if (m < M) {
         double2* dst = part + ((size_t)blockIdx.z * M + m) * M + n0 + c;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (n0 + c + j < M) dst[j] = make_double2((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
+          if (n0 + c + j < M)
+            dst[j] = make_double2((double)__uint_as_float(re[j]),
+                                  (double)__uint_as_float(ia[j]) - (double)__uint_as_float(ib[j]));
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 // lam[m][n] = scale * sum_s part[s][m][n], splits summed in order (deterministic).
@@ -510,7 +528,8 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   if (!tc) {
     double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
     double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
-    k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, nullptr, nullptr);
+    const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
+    k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, none);
     check_launch("k_kb_velocity");
     for (int k = 0; k < M; ++k) {
       const bool last = k == M - 1;
@@ -520,8 +539,8 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
       k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
                                         k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
                                         last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
-                                        last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last, nullptr,
-                                        nullptr, nullptr, nullptr);
+                                        last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last, none,
+                                        none);
       check_launch("k_kb_step");
       prof_end(pe, 7, st);
     }
@@ -543,14 +562,24 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     check_launch("k_kb_reduce");
     return;
   }
-  // tensor-core contraction: chains in FP64 (rolling buffers), stacks in split TF32
+  // tensor-core contraction: chains in FP64 (rolling buffers), stacks in planar split TF32
   double2* Pr = (double2*)h->ws(WS_HALL_P, vb * 3).p;
   auto pbuf = [&](int k) -> double2* { return Pr + (size_t)(k % 3) * total; };
-  float2* Phi = (float2*)h->ws(WS_HALL_B, fb * M * 4).p;
-  float2* Plo = Phi + (size_t)M * total;
-  float2* Bhi = Plo + (size_t)M * total;
-  float2* Blo = Bhi + (size_t)M * total;
-  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), Phi, Plo);
+  const size_t ld = (total + 3) / 4 * 4;
+  const size_t plane = (size_t)M * ld;
+  float* pl = (float*)h->ws(WS_HALL_B, plane * 8 * sizeof(float)).p;
+  if (ld != total) check_cuda(cudaMemsetAsync(pl, 0, plane * 8 * sizeof(float), st), "stack padding");
+  // planes: P re_hi, im_hi, re_lo, im_lo (0..3); B the same (4..7)
+  auto planes = [&](int first, size_t entry) {
+    TcPlanes t;
+    t.re_hi = pl + (first + 0) * plane + entry * ld;
+    t.im_hi = pl + (first + 1) * plane + entry * ld;
+    t.re_lo = pl + (first + 2) * plane + entry * ld;
+    t.im_lo = pl + (first + 3) * plane + entry * ld;
+    return t;
+  };
+  const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
+  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), planes(0, 0));
   check_launch("k_kb_velocity");
   for (int k = 0; k < M; ++k) {
     const bool last = k == M - 1;
@@ -559,29 +588,27 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     const size_t pe = prof_begin(st);
     k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
                                       last ? nullptr : pbuf(k + 1), qk, qkm1, last ? nullptr : qbuf(k + 1), nullptr,
-                                      k == 0, last, last ? nullptr : Phi + (size_t)(k + 1) * total,
-                                      last ? nullptr : Plo + (size_t)(k + 1) * total, Bhi + (size_t)k * total,
-                                      Blo + (size_t)k * total);
+                                      k == 0, last, last ? none : planes(0, k + 1), planes(4, k));
     check_launch("k_kb_step");
     prof_end(pe, 7, st);
   }
-  // splits: contraction chunks of about 16K floats (the FP32 accumulation span)
-  // and at least four waves of one CTA per SM
-  const size_t Kr = 2 * total;
+  // splits: contraction chunks of about 8K sites (the FP32 accumulation span) and
+  // at least four waves of one CTA per SM
   const int tiles = (M + TC_TM - 1) / TC_TM;
-  long long S = std::max<long long>((long long)((Kr + 16383) / 16384),
+  long long S = std::max<long long>((long long)((ld + 8191) / 8192),
                                     (4LL * gqt::sm_count() + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
-  S = std::min<long long>(S, std::max<long long>(1, (long long)(Kr / TC_TK)));
-  const size_t kchunk = ((Kr + S - 1) / S + TC_TK - 1) / TC_TK * TC_TK;
-  S = (long long)((Kr + kchunk - 1) / kchunk);
+  S = std::min<long long>(S, std::max<long long>(1, (long long)(ld / TC_TK)));
+  const size_t kchunk = ((ld + S - 1) / S + TC_TK - 1) / TC_TK * TC_TK;
+  S = (long long)((ld + kchunk - 1) / kchunk);
   double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * mm * sizeof(double2)).p;
+  TcOperands op;
+  const int order[TC_NT] = {0, 2, 1, 3, 4, 6, 5, 7};  // Pre_hi, Pre_lo, Pim_hi, Pim_lo, Bre_hi, Bre_lo, Bim_hi, Bim_lo
+  for (int t = 0; t < TC_NT; ++t) op.plane[t] = pl + order[t] * plane;
   check_cuda(cudaFuncSetAttribute(k_kb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM),
              "smem attribute");
   check_cuda(cudaMemsetAsync(h->d_flag.p, 0, sizeof(int), st), "flag reset");
   const size_t pg = prof_begin(st);
-  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), 128, TC_SMEM, st>>>((const float*)Phi, (const float*)Plo,
-                                                                      (const float*)Bhi, (const float*)Blo, M, Kr,
-                                                                      kchunk, part, (int*)h->d_flag.p);
+  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), 128, TC_SMEM, st>>>(op, M, ld, kchunk, part, (int*)h->d_flag.p);
   check_launch("k_kb_gemm_tc");
   prof_end(pg, 8, st);
   k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M, (double)h->n / R,
