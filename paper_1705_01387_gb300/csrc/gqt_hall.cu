@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ 
 // split of the contraction, splits summed in FP64).  The stacks are planar
 // (real and imaginary planes [M][ld], ld = N R rounded up to 4), so with
 //   Re Lambda = Pre.Bre + Pim.Bim,  Im Lambda = Pre.Bim - Pim.Bre
-// every operand is a plain tile of a plane.  One CTA of 128 threads computes a
+// every operand is a plain tile of a plane.  One CTA of 256 threads computes a
 // 128 x 128 output tile into three accumulators of 128 tensor-memory columns
 // (Re, Pre.Bim, Pim.Bre); contraction stages of 16 sites pass through three
 // shared-memory buffers filled by cp.async two stages ahead of the products.
@@ -233,6 +233,7 @@ constexpr int TC_STAGE = TC_NT * TC_TILE;     // 73,728 B
 constexpr int TC_NBUF = 3;
 constexpr int TC_SMEM = TC_NBUF * TC_STAGE + 64;
 constexpr int TC_WAIT_LIMIT = 1 << 24;
+constexpr int TC_THREADS = 256;  // 8 warps issue the copies; thread 0 the products
 
 struct TcOperands {
   const float* plane[TC_NT];  // same order as the shared-memory tiles
@@ -277,16 +278,17 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// One stage of copies: 8 tiles x 128 rows x 4 chunks of 16 B, four per thread
-// per tile; rows past M and sites past ke are filled with zeros (source size 0).
+// One stage of copies: 8 tiles x 128 rows x 4 chunks of 16 B, two per thread
+// per tile (256 threads); rows past M and sites past ke are filled with zeros
+// (source size 0).
 __device__ __forceinline__ void tc_fill(const TcOperands& op, unsigned char* st, int m0, int n0, int M, size_t ld,
                                         size_t k0, size_t ke) {
 #pragma unroll
   for (int t = 0; t < TC_NT; ++t) {
     const int base = t < 4 ? m0 : n0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = threadIdx.x + 128 * q;
+    for (int q = 0; q < 2; ++q) {
+      const int idx = threadIdx.x + TC_THREADS * q;
       const int row = idx >> 2, kq = idx & 3;
       const size_t k = k0 + 4 * kq;
       const bool valid = base + row < M && k < ke;
@@ -297,7 +299,7 @@ __device__ __forceinline__ void tc_fill(const TcOperands& op, unsigned char* st,
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(TcOperands op, int M, size_t ld, size_t kchunk,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_kb_gemm_tc(TcOperands op, int M, size_t ld, size_t kchunk,
                                                        double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(tc_sm + TC_NBUF * TC_STAGE);
@@ -376,9 +378,13 @@ __global__ void __launch_bounds__(128, 1) k_kb_gemm_tc(TcOperands op, int M, siz
   if (!ok && tid == 0) atomicOr(err, 16);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    const int m = m0 + warp * 32 + (tid & 31);
-    const uint32_t lane = (uint32_t)(warp * 32) << 16;
-    for (int c = 0; c < TC_TM; c += 32) {
+    // warp w reads tensor-memory lanes 32 (w % 4) .. +31; warps 0-3 take columns
+    // 0..63, warps 4-7 columns 64..127
+    const int quarter = warp & 3;
+    const int m = m0 + quarter * 32 + (tid & 31);
+    const uint32_t lane = (uint32_t)(quarter * 32) << 16;
+    const int cbeg = (warp >> 2) * (TC_TM / 2);
+    for (int c = cbeg; c < cbeg + TC_TM / 2; c += 32) {
       uint32_t re[32], ia[32], ib[32];
       tc_ld32(tmem + lane + c, re);
       tc_ld32(tmem + lane + 128 + c, ia);
@@ -608,7 +614,8 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
              "smem attribute");
   check_cuda(cudaMemsetAsync(h->d_flag.p, 0, sizeof(int), st), "flag reset");
   const size_t pg = prof_begin(st);
-  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), 128, TC_SMEM, st>>>(op, M, ld, kchunk, part, (int*)h->d_flag.p);
+  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), TC_THREADS, TC_SMEM, st>>>(op, M, ld, kchunk, part,
+                                                                             (int*)h->d_flag.p);
   check_launch("k_kb_gemm_tc");
   prof_end(pg, 8, st);
   k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M, (double)h->n / R,
