@@ -108,14 +108,29 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
   }
 }
 
+// Velocity hoppings vh_s = d_s * hop2_s of direction b (slot-major like hop2), so
+// that the velocity in k_kb_step costs one multiply-add per slot.
+template <bool CH>
+__global__ void k_kb_vhop(HallEll<CH> H, const double* __restrict__ d, typename HallEll<CH>::HT* __restrict__ vh) {
+  const size_t total = (size_t)H.K * H.n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const auto h = H.hop2[t];
+    if constexpr (CH)
+      vh[t] = make_double2(d[t] * h.x, d[t] * h.y);
+    else
+      vh[t] = d[t] * h;
+  }
+}
+
 // Order k of both chains, element e = i*R + r:
 //   P_{k+1} = 2H~P_k - P_{k-1}   (P_1 = H~P_0 at k = 0), unless last
 //   Q_{k+1} = 2H~Q_k - Q_{k-1}   (Q_1 = H~Q_0),           unless last
-//   B_k = v~_b Q_k                (from the same gathers of Q_k)
+//   B_k = v~_b Q_k                (from the same gathers of Q_k; vh = d_b * hop2)
 // TC: P_{k+1} and B_k also (or, for B_k, only) go to the planar TF32-split stacks
 // (ps: entry k+1, bs: entry k); bout may then be null.
 template <bool CH>
-__global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __restrict__ db, int R, size_t total,
+__global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const typename HallEll<CH>::HT* __restrict__ vh,
+                                                 int R, size_t total,
                                                  const double2* __restrict__ pk, const double2* __restrict__ pkm1,
                                                  double2* __restrict__ pout, const double2* __restrict__ qk,
                                                  const double2* __restrict__ qkm1, double2* __restrict__ qout,
@@ -132,7 +147,7 @@ __global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const double* __
       const auto h2 = H.hop2[sl];
       const double2 qj = qk[j];
       q = mla(q, h2, qj);
-      b = mla(b, h2, make_double2(db[sl] * qj.x, db[sl] * qj.y));
+      b = mla(b, vh[sl], qj);
       if (!last) a = mla(a, h2, pk[j]);
     }
     const double2 bv = make_double2(-0.5 * b.y, 0.5 * b.x);
@@ -531,6 +546,10 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
   auto qbuf = [&](int k) -> double2* { return Q + (size_t)(k % 3) * total; };
   const size_t mm = (size_t)M * M;
+  using HT = typename HallEll<CH>::HT;
+  HT* vh = (HT*)h->ws(WS_HALL_W, (size_t)H.K * H.n * sizeof(HT)).p;
+  k_kb_vhop<CH><<<grid_for((size_t)H.K * H.n), 256, 0, st>>>(H, db, vh);
+  check_launch("k_kb_vhop");
   if (!tc) {
     double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
     double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
@@ -542,7 +561,7 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
       const double2* qk = k == 0 ? r : qbuf(k);
       const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
       const size_t pe = prof_begin(st);
-      k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, Pst + (size_t)k * total,
+      k_kb_step<CH><<<g, 256, 0, st>>>(H, vh, R, total, Pst + (size_t)k * total,
                                         k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
                                         last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
                                         last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last, none,
@@ -592,7 +611,7 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     const double2* qk = k == 0 ? r : qbuf(k);
     const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
     const size_t pe = prof_begin(st);
-    k_kb_step<CH><<<g, 256, 0, st>>>(H, db, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
+    k_kb_step<CH><<<g, 256, 0, st>>>(H, vh, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
                                       last ? nullptr : pbuf(k + 1), qk, qkm1, last ? nullptr : qbuf(k + 1), nullptr,
                                       k == 0, last, last ? none : planes(0, k + 1), planes(4, k));
     check_launch("k_kb_step");

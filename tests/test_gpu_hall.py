@@ -146,14 +146,17 @@ def _gpu_lambda_tc(lat, dE, ph, M, a, b):
 
 @pytest.mark.parametrize("name", ["haldane", "square_phases", "honeycomb_real"])
 @pytest.mark.parametrize("M,R", [(1, 1), (17, 2), (70, 1), (130, 3)])
-def test_kb_moments_tensor_core_contraction(name, M, R):
+@pytest.mark.parametrize("pair", ["xy", "yx", "xx"])
+def test_kb_moments_tensor_core_contraction(name, M, R, pair):
     """Split-TF32 contraction on the tcgen05 tensor cores (three products per pair,
     FP32 accumulation per split, FP64 sum of splits): within 1e-5 of the oracle
     (normalised by the largest moment), including partial 128 x 128 tiles."""
     lat, dE = _model(name)
     ph = S.random_phase(lat.n, R, seed=33)
-    got = _gpu_lambda_tc(lat, dE, ph, M, 0, 1).cpu().numpy()
-    ref = O.Hamiltonian(lat, dE).kb_moments(lat.dx, lat.dy, ph, M)
+    d = {"x": (0, lat.dx), "y": (1, lat.dy)}
+    (a, da), (b, db) = d[pair[0]], d[pair[1]]
+    got = _gpu_lambda_tc(lat, dE, ph, M, a, b).cpu().numpy()
+    ref = O.Hamiltonian(lat, dE).kb_moments(da, db, ph, M)
     err = nerr(got, ref)
     assert err < 1e-5, err
 
