@@ -314,6 +314,14 @@ gqt_status gqt_set_cluster(gqt_ham* ham, int enable);
  * runs one recurrence on r with a dot against l per order. */
 gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
 
+/* Blocked sweep order of the multi-vector kernels (default 1; built-in simple-
+ * cubic lattices whose side is a power of two >= 64): the CTAs walk the x-rows in
+ * strips of 32 y-rows through all z before the next strip, so the +-z neighbour
+ * tiles are re-read from L2 rather than DRAM once an xy-plane of the vectors no
+ * longer fits there.  Results equal the natural order up to the summation order
+ * of the moment dots.  0 walks the sites in index order. */
+gqt_status gqt_set_sweep_order(gqt_ham* ham, int enable);
+
 /* Use CUDA graphs for repeated loops (default 1). */
 gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
 

@@ -72,6 +72,7 @@ _SIGS = {
     "gqt_set_variant": [_P, _I],
     "gqt_set_cluster": [_P, _I],
     "gqt_set_vac_pair": [_P, _I],
+    "gqt_set_sweep_order": [_P, _I],
     "gqt_launch_count": [],
     "gqt_profile_start": [],
     "gqt_probe_fp64": [_P, _P],
@@ -414,6 +415,10 @@ def gqt_set_cluster(ham: Ham, enable: bool):
 
 def gqt_set_vac_pair(ham: Ham, enable: bool):
     _check(lib().gqt_set_vac_pair(ham.ptr, int(bool(enable))))
+
+
+def gqt_set_sweep_order(ham: Ham, enable: bool):
+    _check(lib().gqt_set_sweep_order(ham.ptr, int(bool(enable))))
 
 
 def gqt_set_variant(ham: Ham, variant: int):

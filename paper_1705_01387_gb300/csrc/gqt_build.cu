@@ -384,6 +384,17 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
         for (int64_t i = seg[s]; i < seg[s + 1]; ++i) ss[i] = s;
       upload(h->d_site_seg, ss.data(), ss.size() * 4);
     }
+    // Blocked sweep order for the built-in simple-cubic lattice (side a power of two,
+    // >= 64): the multi-vector kernels walk the x-rows strip by strip -- 32 y-rows,
+    // all z, then the next strip -- so that a site's +-z neighbours are read again
+    // within 2 x 32 x L sites instead of two whole xy-planes, which for large L no
+    // longer stay in L2 (the mapping is in the kernels' site_of).
+    if (lattice->kind == GQT_LATTICE_CUBIC && nseg == 1) {
+      const int64_t L = lattice->L1;
+      int sh = 0;
+      while ((int64_t(1) << sh) < L) ++sh;
+      if (L >= 64 && (int64_t(1) << sh) == L) h->row_shift = sh;
+    }
     h->d_flag.ensure(16);
     check_cuda(cudaMemset(h->d_flag.p, 0, 16), "memset");
     check_cuda(cudaMallocHost((void**)&h->h_flag, 16), "cudaMallocHost");

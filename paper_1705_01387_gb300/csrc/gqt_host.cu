@@ -486,6 +486,7 @@ static Ell<FP64, CH> ell_of(const gqt_ham* h) {
   e.hop2 = (const typename Ell<FP64, CH>::HT*)h->d_hop.p;
   e.diag2 = (const typename Ell<FP64, CH>::S*)h->d_diag.p;
   e.dx = (const typename Ell<FP64, CH>::S*)h->d_dx.p;
+  e.row_shift = (h->use_sweep_order && h->row_shift > 0) ? h->row_shift : 0;
   return e;
 }
 
@@ -1097,6 +1098,13 @@ gqt_status gqt_set_vac_pair(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_pair = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_sweep_order(gqt_ham* h, int enable) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  h->use_sweep_order = enable != 0;
   API_END
 }
 

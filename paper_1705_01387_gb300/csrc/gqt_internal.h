@@ -84,6 +84,8 @@ struct gqt_ham {
   std::vector<int64_t> seg;  // nseg + 1 offsets
   gqt::DevBuf d_idx, d_hop, d_diag, d_dx, d_site_seg, d_flag;
   gqt::DevBuf d_dy;     // FP64 slot-major y displacements (Hall moments), when the model defines them
+  int row_shift = 0;       // blocked sweep order (built-in cubic lattices): log2 of the side, 0 = off
+  bool use_sweep_order = true;
   bool has_dy = false;
   int* h_flag = nullptr;  // pinned
   int threads = 256;

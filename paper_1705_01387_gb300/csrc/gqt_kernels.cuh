@@ -57,7 +57,22 @@ struct Ell {
   const HT* __restrict__ hop2;
   const S* __restrict__ diag2;
   const S* __restrict__ dx;
+  // optional blocked sweep order of the multi-vector kernels for a simple-cubic
+  // lattice of side L = 2^row_shift (0: sites in index order), see site_of
+  int row_shift;
 };
+
+// Site visited at wave position w.  Blocked order (row_shift = log2 L > 0): the
+// x-rows are walked in strips of 32 y-rows through all z, i.e. w = x + L (yy +
+// 32 (z + L yb)) visits site x + L (32 yb + yy) + L^2 z.  Shifts and masks only.
+template <class E>
+__device__ __forceinline__ int site_of(const E& H, int w) {
+  const int lx = H.row_shift;
+  if (lx == 0) return w;
+  const int m = (1 << lx) - 1;
+  const int r = w >> lx, t = r >> 5;
+  return (w & m) | ((((t >> lx) << 5) | (r & 31)) << lx) | ((t & m) << (2 * lx));
+}
 
 // ---------------------------------------------------------------- arithmetic
 
@@ -1429,7 +1444,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
   HT phop{};
   auto fetch_next = [&](size_t gn) {
     if (gn < ge) {
-      const int i = (int)(gn >> gs);
+      const int i = site_of(H, (int)(gn >> gs));
       if (lg < KK) {
         const size_t s = (size_t)lg * H.n + i;
         pidx = __ldg(H.idx + s);
@@ -1458,7 +1473,7 @@ __device__ __forceinline__ void cheb_wave_vpt(const Ell<FP64, CH>& H, int4 tb, i
       dg = get_re(shfl_g(chop, KK, G));
     }
     if (gi >= ge) continue;
-    const int i = (int)(gi >> gs);
+    const int i = site_of(H, (int)(gi >> gs));
     const int r0 = lane_offset<FP64>(lg);
     const size_t base = (size_t)i * R + r0;
     V own[VPT], acc[VPT], lv[VPT];
@@ -1608,7 +1623,7 @@ __device__ __forceinline__ void cheb_pair_vpt(const Ell<FP64, CH>& H, int4 tb, i
   HT phop{};
   auto fetch_next = [&](size_t gn) {
     if (gn < ge) {
-      const int i = (int)(gn >> gs);
+      const int i = site_of(H, (int)(gn >> gs));
       if (lg < KK) {
         const size_t s = (size_t)lg * H.n + i;
         pidx = __ldg(H.idx + s);
@@ -1637,7 +1652,7 @@ __device__ __forceinline__ void cheb_pair_vpt(const Ell<FP64, CH>& H, int4 tb, i
       dg = get_re(shfl_g(chop, KK, G));
     }
     if (gi >= ge) continue;
-    const int i = (int)(gi >> gs);
+    const int i = site_of(H, (int)(gi >> gs));
     const int r0 = lane_offset<FP64>(lg);
     const size_t base = (size_t)i * R + r0;
     if constexpr (!PF) {

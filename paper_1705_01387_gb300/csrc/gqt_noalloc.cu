@@ -82,6 +82,7 @@ Ell<FP64, CH> ell_view(const gqt_ham* h) {
   e.hop2 = (const typename Ell<FP64, CH>::HT*)h->d_hop.p;
   e.diag2 = (const typename Ell<FP64, CH>::S*)h->d_diag.p;
   e.dx = (const typename Ell<FP64, CH>::S*)h->d_dx.p;
+  e.row_shift = 0;
   return e;
 }
 

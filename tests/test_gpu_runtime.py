@@ -390,3 +390,39 @@ def test_vac_pair_rows_match_oracle(name, R, M):
                 assert nerr(got[False][k, q, r], ref[k]) < tol
     if prec == g.GQT_FP64:
         assert nerr(got[True], got[False]) < 1e-12
+
+
+@pytest.mark.parametrize("R,prec", [(32, "fp32"), (16, "fp32"), (8, "fp64")])
+def test_blocked_sweep_order_cubic(R, prec):
+    """Built-in simple-cubic lattice with a power-of-two side (L = 64): the
+    multi-vector kernels walk the sites strip by strip (32 y-rows through all z).
+    DOS and VAC moments equal the natural order (up to the summation order of the
+    dots) and, for sampled vectors, the oracle on the same lattice."""
+    L = 64
+    p = g.GQT_FP32_ACC64 if prec == "fp32" else g.GQT_FP64
+    dE = S.energy_scale_rule(6, -1.0, 16.5)
+    ham = g.gqt_build_hamiltonian(None, dE, p, kind=g.GQT_LATTICE_CUBIC, L1=L, t=-1.0, W=16.5, seed=17)
+    if prec == "fp64":
+        g.gqt_set_launch(ham, 128, 0)  # the multi-vector kernels
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    phi = torch.empty((ham.n, R), dtype=cd, device="cuda")
+    g.gqt_random_phase(ham, 5, R, phi)
+    M = 40
+    dts = np.array([0.4])
+    Np = [O.np_rule(dE * 0.4, 64)]
+    got = {}
+    for order in (True, False):
+        g.gqt_set_sweep_order(ham, order)
+        mu = np.empty((1, R, M))
+        g.gqt_dos_moments(ham, phi, R, M, mu)
+        got[order] = (mu, _vac(ham, phi, dts, M, Np))
+    tol_same = 1e-5 if prec == "fp32" else 1e-13
+    assert nerr(got[True][0], got[False][0]) < tol_same
+    assert nerr(got[True][1], got[False][1]) < tol_same
+    lat = S.cubic(L, -1.0, 16.5, seed=17)
+    h = O.Hamiltonian(lat, dE)
+    ph = phi.cpu().numpy().astype(np.complex128)
+    tol = 2e-5 if prec == "fp32" else 1e-10
+    for r in (0, R - 1):
+        assert nerr(got[True][0][0, r], h.dos_moments(ph[:, r], M)) < tol
+        assert nerr(got[True][1][0, 0, r], h.vac_moments(ph[:, r], dts, Np, M)[0]) < (1e-4 if prec == "fp32" else 1e-10)
