@@ -281,8 +281,9 @@ int gqt_np_rule(double x, int cap);
 
 /* Kernel launch shape for a handle: threads per block and blocks per SM of the
  * Chebyshev kernels (0 = library default).  gqt_autotune times every variant x
- * threads x blocks-per-SM candidate on zero-filled scratch vectors (a few
- * Re <l|T_m|r> orders for the given R) and keeps the fastest. */
+ * threads x blocks-per-SM candidate (0, the per-kernel default, among them) on
+ * zero-filled scratch vectors (a few Re <l|T_m|r> orders for the given R) and
+ * keeps the fastest. */
 gqt_status gqt_set_launch(gqt_ham* ham, int threads, int blocks_per_sm);
 /* Moment-kernel variant: 0 = each CTA walks one contiguous chunk of sites; 1 =
  * wavefront order (the CTAs of a segment stride through it together, so

@@ -1587,7 +1587,7 @@ extern "C" gqt_status gqt_autotune(gqt_ham* h, int R, int* threads, int* blocks_
   check_cuda(cudaMemsetAsync(x, 0, vb, st), "memset");
   check_cuda(cudaMemsetAsync(l, 0, vb, st), "memset");
   const int cand_t[] = {128, 256, 512};
-  const int cand_b[] = {2, 4, 8};
+  const int cand_b[] = {0, 2, 4, 8};  // 0: each kernel's own resident-CTA count (the default)
   const int cand_v[] = {0, 1, 2, 3};
   const int M = 12;
   DevBuf scratch_mu;
