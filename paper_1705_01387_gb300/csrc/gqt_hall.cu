@@ -66,13 +66,14 @@ __device__ __forceinline__ double2 mla(double2 acc, double2 h, double2 x) {
 }
 
 // Split of an FP64 value into two TF32 numbers (FP32 with the low 13 mantissa
-// bits zero, as the tensor cores read them): hi = x rounded to TF32, lo = x - hi
-// rounded to FP32 (the tensor cores keep its top 11 bits).  hi + lo carries about
-// 22 significant bits.
+// bits zero, as the tensor cores read them): f = x rounded to FP32, hi = f rounded
+// to TF32, lo = f - hi (exact in FP32; the tensor cores keep its top 11 bits).
+// hi + lo carries about 22 significant bits; the FP32 rounding of x (2^-24) is
+// below that, and forming lo from f keeps the split to one FP64-pipe conversion.
 __device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
   const float f = (float)x;
   hi = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
-  lo = (float)(x - (double)hi);
+  lo = f - hi;
 }
 // Planar TF32-split stack entry: re_hi, im_hi, re_lo, im_lo planes (null re_hi: none).
 struct TcPlanes {
