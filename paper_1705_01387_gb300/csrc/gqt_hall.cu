@@ -624,6 +624,7 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   long long S = std::max<long long>((long long)((ld + 8191) / 8192),
                                     (4LL * gqt::sm_count() + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
   S = std::min<long long>(S, std::max<long long>(1, (long long)(ld / TC_TK)));
+  S = std::min<long long>(S, 65535);  // gridDim.z limit (longer splits beyond N R ~ 5e8)
   const size_t kchunk = ((ld + S - 1) / S + TC_TK - 1) / TC_TK * TC_TK;
   S = (long long)((ld + kchunk - 1) / kchunk);
   double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * mm * sizeof(double2)).p;
