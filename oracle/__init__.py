@@ -78,6 +78,8 @@ def lib():
             L.orc_vac_loss_grad.argtypes = [C.c_void_p, _d, _d, _ip, C.c_int, C.c_int, _d, _d, _d]
             L.orc_kb_moments.argtypes = [C.c_void_p, _d, _d, _d, C.c_int, C.c_int, _d]
             L.orc_kubo_bastin.argtypes = [_d, C.c_int, _d, C.c_int, C.c_double, C.c_double, C.c_int, _d]
+            L.orc_kubo_bastin_fermi.argtypes = [_d, C.c_int, _d, C.c_int, C.c_double, C.c_double, C.c_int, _d,
+                                                C.c_int, C.c_double, _d]
             _lib = L
     return _lib
 
@@ -264,4 +266,16 @@ def kubo_bastin(lam, E, energy_scale, area, kernel=0):
     out = np.empty(E.size, np.float64)
     lib().orc_kubo_bastin(lam.view(np.float64).reshape(-1), lam.shape[0], E, E.size, float(energy_scale),
                           float(area), int(kernel), out)
+    return out
+
+
+def kubo_bastin_fermi(lam, E, energy_scale, area, mu, kT, kernel=0):
+    """sigma_ab(mu_j, T) / (e^2/h): the Kubo-Bastin integrand on the ascending grid E
+    weighted by the Fermi function 1/(1 + exp((E - mu_j)/kT)) (kT = 0: step)."""
+    lam = np.ascontiguousarray(lam, np.complex128)
+    E = np.ascontiguousarray(E, np.float64)
+    mu = np.ascontiguousarray(np.atleast_1d(mu), np.float64)
+    out = np.empty(mu.size, np.float64)
+    lib().orc_kubo_bastin_fermi(lam.view(np.float64).reshape(-1), lam.shape[0], E, E.size, float(energy_scale),
+                                float(area), int(kernel), mu, mu.size, float(kT), out)
     return out

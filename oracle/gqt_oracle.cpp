@@ -534,6 +534,29 @@ void apply_vd(const Ham& h, const double* d, const cplx* x, cplx* y) {
   }
 }
 
+// F(x_j) = (1 - x^2)^{-2} Re sum_mn c_m c_n g_m g_n Gamma_mn(x) Lambda_mn at x_j = E_j/dE.
+std::vector<double> kb_integrand(const double* lam, int M, const double* E, int NE, double dE, int kernel) {
+  const cplx I(0.0, 1.0);
+  std::vector<double> w(M);
+  for (int n = 0; n < M; ++n) w[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0 ? jackson(n, M) : 1.0);
+  std::vector<double> F(NE);
+  for (int j = 0; j < NE; ++j) {
+    const double x = E[j] / dE;
+    const double th = std::acos(x);
+    const double s = std::sin(th);
+    cplx acc = 0.0;
+    for (int m = 0; m < M; ++m)
+      for (int n = 0; n < M; ++n) {
+        const cplx g = std::cos(m * th) * std::exp(-I * (double)n * th) * (x + I * (double)n * s) +
+                       std::cos(n * th) * std::exp(I * (double)m * th) * (x - I * (double)m * s);
+        const cplx l(lam[2 * ((size_t)m * M + n)], lam[2 * ((size_t)m * M + n) + 1]);
+        acc += w[m] * w[n] * g * l;
+      }
+    F[j] = acc.real() / ((1.0 - x * x) * (1.0 - x * x));
+  }
+  return F;
+}
+
 // T_0 x .. T_{M-1} x by the three-term recursion (Eq. 21).
 std::vector<std::vector<cplx>> cheb_vectors(const Ham& h, const cplx* x, int M) {
   std::vector<std::vector<cplx>> T(M, std::vector<cplx>(h.n));
@@ -587,28 +610,35 @@ void orc_kb_moments(const orc_ham* hp, const double* d_a, const double* d_b, con
 // Jackson, 1 = none.  area = Omega.
 void orc_kubo_bastin(const double* lam, int M, const double* E, int NE, double dE, double area, int kernel,
                      double* sigma) {
-  const cplx I(0.0, 1.0);
-  std::vector<double> w(M);
-  for (int n = 0; n < M; ++n) w[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0 ? jackson(n, M) : 1.0);
-  std::vector<double> F(NE);
-  for (int j = 0; j < NE; ++j) {
-    const double x = E[j] / dE;
-    const double th = std::acos(x);
-    const double s = std::sin(th);
-    cplx acc = 0.0;
-    for (int m = 0; m < M; ++m)
-      for (int n = 0; n < M; ++n) {
-        const cplx g = std::cos(m * th) * std::exp(-I * (double)n * th) * (x + I * (double)n * s) +
-                       std::cos(n * th) * std::exp(I * (double)m * th) * (x - I * (double)m * s);
-        const cplx l(lam[2 * ((size_t)m * M + n)], lam[2 * ((size_t)m * M + n) + 1]);
-        acc += w[m] * w[n] * g * l;
-      }
-    F[j] = acc.real() / ((1.0 - x * x) * (1.0 - x * x));
-  }
+  const std::vector<double> F = kb_integrand(lam, M, E, NE, dE, kernel);
   double run = 0.0;
   for (int j = 0; j < NE; ++j) {
     if (j > 0) run += 0.5 * (E[j] - E[j - 1]) / dE * (F[j] + F[j - 1]);
     sigma[j] = 2.0 / area * run;
+  }
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Finite-temperature Hall conductivity: sigma_ab(mu_j, T)/(e^2/h) =
+// (2/Omega) int dx f((E - mu_j)/kT) F(x), f(u) = 1/(1 + e^u) the Fermi function,
+// with F(x) as in orc_kubo_bastin on the ascending energy grid E (the trapezoid
+// rule over the grid; kT in the units of E, kT = 0 the step function with
+// f(0) = 1/2).
+void orc_kubo_bastin_fermi(const double* lam, int M, const double* E, int NE, double dE, double area, int kernel,
+                           const double* mu, int Nmu, double kT, double* sigma) {
+  const std::vector<double> F = kb_integrand(lam, M, E, NE, dE, kernel);
+  for (int q = 0; q < Nmu; ++q) {
+    auto fermi = [&](double e) {
+      if (kT <= 0.0) return e < mu[q] ? 1.0 : (e > mu[q] ? 0.0 : 0.5);
+      return 1.0 / (1.0 + std::exp((e - mu[q]) / kT));
+    };
+    double run = 0.0;
+    for (int j = 1; j < NE; ++j)
+      run += 0.5 * (E[j] - E[j - 1]) / dE * (fermi(E[j]) * F[j] + fermi(E[j - 1]) * F[j - 1]);
+    sigma[q] = 2.0 / area * run;
   }
 }
 

@@ -45,6 +45,9 @@ MUTATIONS = [
      "std::exp(I * (double)n * th) * (x + I * (double)n * s)"),
     ("Kubo-Bastin (2 - delta) dropped", "w[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0", "w[n] = (1.0) * (kernel == 0"),
     ("Kubo-Bastin prefactor 2/Omega", "sigma[j] = 2.0 / area * run;", "sigma[j] = 1.0 / area * run;"),
+    ("Fermi function sign", "return 1.0 / (1.0 + std::exp((e - mu[q]) / kT));",
+     "return 1.0 / (1.0 + std::exp((mu[q] - e) / kT));"),
+    ("Fermi step half weight", "e > mu[q] ? 0.0 : 0.5", "e > mu[q] ? 0.0 : 1.0"),
 ]
 
 PINS = [
@@ -65,6 +68,7 @@ PINS = [
     lambda: P.test_kb_moments_match_exact_trace("xy"),
     lambda: P.test_kb_moments_vanish_by_mirror_symmetry(),
     lambda: P.test_kubo_bastin_reconstruction_closed_forms(),
+    lambda: P.test_kubo_bastin_fermi_limits_and_quadrature(),
 ]
 
 

@@ -521,3 +521,31 @@ def test_kubo_bastin_haldane_chern_plateau(mass, chern):
     E = np.linspace(-0.97 * dE, 0.0, 3001)
     sig = O.kubo_bastin(lam, E, dE, lat.volume)
     assert abs(sig[-1] - exact) < 1e-2
+
+
+def test_kubo_bastin_fermi_limits_and_quadrature():
+    """Finite temperature: at kT = 0 on a uniform grid the Fermi-weighted trapezoid
+    sum at an interior grid energy mu = E_j equals the zero-temperature integral
+    to E_j exactly (the half weight at E = mu splits the last interval evenly); for Lambda_00 = 1,
+    F = 2x/(1-x^2)^2 and sigma(mu, T) agrees with an adaptive quadrature of
+    (2/Omega) f((dE x - mu)/kT) F(x) (scipy), and rises with mu."""
+    from scipy import integrate
+    rng = np.random.default_rng(9)
+    M, dE, area = 21, 2.5, 4.0
+    lam = (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))) / (1 + np.arange(M))[None, :]
+    E = np.linspace(-0.9 * dE, 0.9 * dE, 2001)
+    zero = O.kubo_bastin(lam, E, dE, area)
+    idx = np.array([1, 500, 1000, 1777, 1999])  # interior grid points (an end has one neighbouring interval)
+    step = O.kubo_bastin_fermi(lam, E, dE, area, E[idx], 0.0)
+    assert np.max(np.abs(step - zero[idx])) <= 1e-12 * np.max(np.abs(zero))
+    lam0 = np.zeros((3, 3), np.complex128)
+    lam0[0, 0] = 1.0
+    E = np.linspace(-0.8 * dE, 0.8 * dE, 40001)
+    mus = np.array([-0.6, -0.1, 0.0, 0.3, 1.2])
+    kT = 0.05
+    got = O.kubo_bastin_fermi(lam0, E, dE, area, mus, kT)
+    for q, mu in enumerate(mus):
+        f = lambda x: 2.0 / area * 2 * x / (1 - x * x) ** 2 / (1 + np.exp(np.clip((dE * x - mu) / kT, -700, 700)))
+        ref, _ = integrate.quad(f, E[0] / dE, E[-1] / dE, points=[mu / dE], limit=400, epsabs=1e-13, epsrel=1e-12)
+        assert abs(got[q] - ref) < 1e-6 * (1 + abs(ref))
+    assert np.all(np.diff(got[mus > 0]) > 0)  # F > 0 for x > 0: more states filled, larger sigma
