@@ -243,6 +243,16 @@ gqt_status gqt_set_kb_contraction(gqt_ham* ham, int mode);
 gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale, double area,
                            int kernel, double* d_sigma, void* stream);
 
+/* sigma_ab(mu_q, T) in units of e^2/h at temperature kT (same units as E):
+ * (2/area) int dx f((E - mu_q)/kT) F(x) with F as in gqt_kubo_bastin and the
+ * Fermi function f(u) = 1/(1 + e^u) (kT = 0: the step, 1/2 at E = mu), by the
+ * trapezoid rule over the ascending grid d_E [NE] (NE >= 2, |E| < dE; it should
+ * cover the spectrum and a few kT above the largest mu).  d_mu [Nmu], d_sigma
+ * [Nmu], d_lambda [M][M] complex: device FP64.  Synchronises the stream. */
+gqt_status gqt_kubo_bastin_fermi(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,
+                                 double area, int kernel, const double* d_mu, int Nmu, double kT, double* d_sigma,
+                                 void* stream);
+
 /* Running conductivity from the VAC (Eq. 2): sigma[k][e] = sum_{j<k} dt[j] (v[j][e] + v[j+1][e]) / 2
  * over rows at t_0 = 0 .. t_{Nt-1} of rho*C_vv (device [Nt][NE]); dt host [Nt]. */
 gqt_status gqt_sigma_vac(const double* d_vac, const double* dt, int Nt, int NE, double* d_sigma, void* stream);

@@ -59,6 +59,7 @@ _SIGS = {
     "gqt_kb_moments": [_P, _P, _I, _I, _I, _I, _P, _P],
     "gqt_set_kb_contraction": [_P, _I],
     "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
+    "gqt_kubo_bastin_fermi": [_P, _I, _P, _I, _D, _D, _I, _P, _I, _D, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
     "gqt_bond_gradients": [_P, _I64, _P, _P, _I, _P, _P, _P],
     "gqt_sigma_vac": [_P, _P, _I, _I, _P, _P],
@@ -341,6 +342,16 @@ def gqt_kubo_bastin(lam, E, energy_scale: float, area: float, sigma, kernel: int
     _check(lib().gqt_kubo_bastin(_dptr(lam, "lam"), int(lam.shape[0]), _dptr(E, "E"), int(E.numel()),
                                  float(energy_scale), float(area), int(kernel), _dptr(sigma, "sigma"),
                                  _stream(stream)))
+    return sigma
+
+
+def gqt_kubo_bastin_fermi(lam, E, energy_scale: float, area: float, mu, kT: float, sigma, kernel: int = 0,
+                          stream=None):
+    """sigma_ab(mu, T) / (e^2/h) (CUDA float64 [Nmu]) at chemical potentials mu (CUDA float64
+    [Nmu]) and temperature kT from moments lam on the ascending energy grid E."""
+    _check(lib().gqt_kubo_bastin_fermi(_dptr(lam, "lam"), int(lam.shape[0]), _dptr(E, "E"), int(E.numel()),
+                                       float(energy_scale), float(area), int(kernel), _dptr(mu, "mu"),
+                                       int(mu.numel()), float(kT), _dptr(sigma, "sigma"), _stream(stream)))
     return sigma
 
 

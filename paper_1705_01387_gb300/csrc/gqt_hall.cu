@@ -521,6 +521,28 @@ __global__ void k_kb_scan(const double* __restrict__ F, const double* __restrict
   }
 }
 
+// sigma(mu_q, T) = pref * sum_k (x_{k+1} - x_k)(f_k F_k + f_{k+1} F_{k+1})/2 with the
+// Fermi weights f_k = 1/(1 + exp((E_k - mu_q)/kT)) (kT = 0: the step, 1/2 at E = mu);
+// one thread per chemical potential.
+__global__ void k_kb_fermi(const double* __restrict__ F, const double* __restrict__ E, int NE, double inv_dE,
+                           const double* __restrict__ mu, int Nmu, double kT, double pref,
+                           double* __restrict__ sigma) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Nmu) return;
+  const double m = mu[q];
+  auto fermi = [&](double e) {
+    if (kT <= 0.0) return e < m ? 1.0 : (e > m ? 0.0 : 0.5);
+    return 1.0 / (1.0 + exp((e - m) / kT));
+  };
+  double run = 0.0, prev = fermi(E[0]) * F[0];
+  for (int j = 1; j < NE; ++j) {
+    const double cur = fermi(E[j]) * F[j];
+    run += 0.5 * (E[j] - E[j - 1]) * inv_dE * (prev + cur);
+    prev = cur;
+  }
+  sigma[q] = pref * run;
+}
+
 double jackson_g(int n, int M) {
   const double a = 1.0 / (M + 1.0), pi = 3.14159265358979323846;
   return (1.0 - n * a) * std::cos(pi * n * a) + a * std::sin(pi * n * a) / std::tan(pi * a);
@@ -542,7 +564,7 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
   H.diag2 = (const double*)h->d_diag.p;
   const bool tc = h->kb_mode == 1;
   const size_t total = (size_t)h->n * R;
-  const size_t vb = total * sizeof(double2), fb = total * sizeof(float2);
+  const size_t vb = total * sizeof(double2);
   const int g = grid_for(total);
   double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
   auto qbuf = [&](int k) -> double2* { return Q + (size_t)(k % 3) * total; };
@@ -689,6 +711,57 @@ extern "C" gqt_status gqt_set_kb_contraction(gqt_ham* h, int mode) {
   return GQT_OK;
 }
 
+// Device F (the Kubo-Bastin integrand) on the energy grid into buf + M (buf: M
+// weights then NE values); returns an error code of the launches.
+static cudaError_t kb_integrand_dev(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,
+                                    int kernel, double* buf, cudaStream_t st) {
+  std::vector<double> hw(M);
+  for (int n = 0; n < M; ++n) hw[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0 ? jackson_g(n, M) : 1.0);
+  // energies per CTA: as many as keep the tables (24 B per energy and moment) within 200 KB
+  const int EB = (size_t)4 * M * 24 <= 200 * 1024 ? 4 : ((size_t)2 * M * 24 <= 200 * 1024 ? 2 : 1);
+  const size_t smem = (size_t)EB * M * (sizeof(double) + sizeof(double2));
+  const void* kern = EB == 4 ? (const void*)k_kb_integrand<4>
+                             : (EB == 2 ? (const void*)k_kb_integrand<2> : (const void*)k_kb_integrand<1>);
+  cudaError_t err = cudaSuccess;
+  if (smem > 48 * 1024) err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  double* w = buf;
+  double* F = buf + M;
+  const double inv = 1.0 / energy_scale;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(w, hw.data(), M * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) {
+    // the host copy of the weights must outlive the copy: wait for it here
+    err = cudaStreamSynchronize(st);
+  }
+  if (err == cudaSuccess) {
+    const dim3 grid((NE + EB - 1) / EB);
+    const double2* lam = (const double2*)d_lambda;
+    const size_t pi = prof_begin(st);
+    if (EB == 4)
+      k_kb_integrand<4><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+    else if (EB == 2)
+      k_kb_integrand<2><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+    else
+      k_kb_integrand<1><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) {
+      check_launch("k_kb_integrand");
+      prof_end(pi, 9, st);
+    }
+  }
+  return err;
+}
+
+static std::vector<double> check_energies(const double* d_E, int NE, double energy_scale, cudaStream_t st) {
+  std::vector<double> hE(NE);
+  check_cuda(cudaMemcpyAsync(hE.data(), d_E, NE * sizeof(double), cudaMemcpyDeviceToHost, st), "energies");
+  check_cuda(cudaStreamSynchronize(st), "energies");
+  for (int j = 0; j < NE; ++j) {
+    if (!(std::fabs(hE[j]) < energy_scale)) throw Error(GQT_EINVAL, "Kubo-Bastin: |E| must be < dE");
+    if (j > 0 && !(hE[j] > hE[j - 1])) throw Error(GQT_EINVAL, "Kubo-Bastin: energies must ascend");
+  }
+  return hE;
+}
+
 extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,
                                       double area, int kernel, double* d_sigma, void* stream) {
   try {
@@ -696,51 +769,53 @@ extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const doubl
         kernel < 0 || kernel > 1)
       throw Error(GQT_EINVAL, "gqt_kubo_bastin: bad argument");
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<double> hE(NE);
-    check_cuda(cudaMemcpyAsync(hE.data(), d_E, NE * sizeof(double), cudaMemcpyDeviceToHost, st), "energies");
-    check_cuda(cudaStreamSynchronize(st), "energies");
-    for (int j = 0; j < NE; ++j) {
-      if (!(std::fabs(hE[j]) < energy_scale)) throw Error(GQT_EINVAL, "gqt_kubo_bastin: |E| must be < dE");
-      if (j > 0 && !(hE[j] > hE[j - 1])) throw Error(GQT_EINVAL, "gqt_kubo_bastin: energies must ascend");
-    }
-    std::vector<double> hw(M);
-    for (int n = 0; n < M; ++n) hw[n] = (n == 0 ? 1.0 : 2.0) * (kernel == 0 ? jackson_g(n, M) : 1.0);
-    // energies per CTA: as many as keep the tables (24 B per energy and moment) within 200 KB
-    const int EB = (size_t)4 * M * 24 <= 200 * 1024 ? 4 : ((size_t)2 * M * 24 <= 200 * 1024 ? 2 : 1);
-    const size_t smem = (size_t)EB * M * (sizeof(double) + sizeof(double2));
-    const void* kern = EB == 4 ? (const void*)k_kb_integrand<4>
-                               : (EB == 2 ? (const void*)k_kb_integrand<2> : (const void*)k_kb_integrand<1>);
-    if (smem > 48 * 1024)
-      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute");
+    check_energies(d_E, NE, energy_scale, st);
     // device scratch owned by this call (no handle): weights and F
     double* buf = nullptr;
     check_cuda(cudaMallocAsync((void**)&buf, (size_t)(M + NE) * sizeof(double), st), "cudaMallocAsync");
-    double* w = buf;
-    double* F = buf + M;
-    const double inv = 1.0 / energy_scale;
-    cudaError_t err = cudaMemcpyAsync(w, hw.data(), M * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaError_t err = kb_integrand_dev(d_lambda, M, d_E, NE, energy_scale, kernel, buf, st);
     if (err == cudaSuccess) {
-      const dim3 grid((NE + EB - 1) / EB);
-      const double2* lam = (const double2*)d_lambda;
-      const size_t pi = prof_begin(st);
-      if (EB == 4)
-        k_kb_integrand<4><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
-      else if (EB == 2)
-        k_kb_integrand<2><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
-      else
-        k_kb_integrand<1><<<grid, 256, smem, st>>>(lam, M, d_E, NE, inv, w, F);
+      k_kb_scan<<<1, 32, 0, st>>>(buf + M, d_E, NE, 1.0 / energy_scale, 2.0 / area, d_sigma);
       err = cudaGetLastError();
-      if (err == cudaSuccess) {
-        check_launch("k_kb_integrand");
-        prof_end(pi, 9, st);
-        k_kb_scan<<<1, 32, 0, st>>>(F, d_E, NE, inv, 2.0 / area, d_sigma);
-        err = cudaGetLastError();
-        if (err == cudaSuccess) check_launch("k_kb_scan");
-      }
+      if (err == cudaSuccess) check_launch("k_kb_scan");
     }
     cudaFreeAsync(buf, st);
     check_cuda(err, "gqt_kubo_bastin");
     check_cuda(cudaStreamSynchronize(st), "gqt_kubo_bastin");
+    return GQT_OK;
+  } catch (const Error& e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return GQT_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(std::string("internal error: ") + e.what());
+    return GQT_ECUDA;
+  }
+}
+
+extern "C" gqt_status gqt_kubo_bastin_fermi(const double* d_lambda, int M, const double* d_E, int NE,
+                                            double energy_scale, double area, int kernel, const double* d_mu, int Nmu,
+                                            double kT, double* d_sigma, void* stream) {
+  try {
+    if (!d_lambda || !d_E || !d_mu || !d_sigma || M < 1 || M > 8192 || NE < 2 || Nmu < 1 || !(energy_scale > 0) ||
+        !(area > 0) || kernel < 0 || kernel > 1 || !(kT >= 0) || !std::isfinite(kT))
+      throw Error(GQT_EINVAL, "gqt_kubo_bastin_fermi: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    check_energies(d_E, NE, energy_scale, st);
+    double* buf = nullptr;
+    check_cuda(cudaMallocAsync((void**)&buf, (size_t)(M + NE) * sizeof(double), st), "cudaMallocAsync");
+    cudaError_t err = kb_integrand_dev(d_lambda, M, d_E, NE, energy_scale, kernel, buf, st);
+    if (err == cudaSuccess) {
+      k_kb_fermi<<<(Nmu + 127) / 128, 128, 0, st>>>(buf + M, d_E, NE, 1.0 / energy_scale, d_mu, Nmu, kT, 2.0 / area,
+                                                    d_sigma);
+      err = cudaGetLastError();
+      if (err == cudaSuccess) check_launch("k_kb_fermi");
+    }
+    cudaFreeAsync(buf, st);
+    check_cuda(err, "gqt_kubo_bastin_fermi");
+    check_cuda(cudaStreamSynchronize(st), "gqt_kubo_bastin_fermi");
     return GQT_OK;
   } catch (const Error& e) {
     set_error(e.what());

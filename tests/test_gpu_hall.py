@@ -192,3 +192,34 @@ def test_kb_moments_tensor_core_full_size_lattice():
     ref = O.Hamiltonian(lat, dE).kb_moments(lat.dx, lat.dy, ph, M)
     err = nerr(got, ref)
     assert err < 5e-5, err
+
+
+@pytest.mark.parametrize("kT", [0.0, 0.05, 0.3])
+def test_kubo_bastin_fermi_matches_oracle(kT):
+    rng = np.random.default_rng(6)
+    M, dE, area = 37, 3.7, 12.5
+    lam = (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))) / (1 + np.arange(M))[None, :]
+    E = np.linspace(-0.95 * dE, 0.9 * dE, 1201)
+    mu = np.array([-2.0, -0.5, 0.0, E[600], 1.7])
+    sig = torch.empty(mu.size, dtype=torch.float64, device="cuda")
+    g.gqt_kubo_bastin_fermi(torch.from_numpy(lam).cuda(), torch.from_numpy(E).cuda(), dE, area,
+                            torch.from_numpy(mu).cuda(), kT, sig)
+    ref = O.kubo_bastin_fermi(lam, E, dE, area, mu, kT)
+    assert nerr(sig.cpu().numpy(), ref) < 1e-10
+
+
+def test_haldane_plateau_finite_temperature():
+    """At kT = 0.02 (gap about 1.7 wide) sigma_xy at the gap centre stays the Chern
+    number; well inside the band, temperature changes it."""
+    lat = S.haldane(8, 8, -1.0, 0.15, math.pi / 2, 0.0, 0.0)
+    dE = 1.05 * (3.0 + 6 * 0.15)
+    lam = _gpu_lambda(lat, dE, np.eye(lat.n, dtype=np.complex128), 256, 0, 1)
+    E = torch.from_numpy(np.linspace(-0.97 * dE, 0.97 * dE, 4001)).cuda()
+    mu = torch.tensor([0.0, -1.9], dtype=torch.float64, device="cuda")
+    out = {}
+    for kT in (0.0, 0.02, 0.3):
+        sig = torch.empty(2, dtype=torch.float64, device="cuda")
+        g.gqt_kubo_bastin_fermi(lam, E, dE, lat.volume, mu, kT, sig)
+        out[kT] = sig.cpu().numpy()
+    assert abs(out[0.02][0] - 1.0) < 1e-2 and abs(out[0.0][0] - 1.0) < 1e-2
+    assert abs(out[0.3][1] - out[0.0][1]) > 1e-3
