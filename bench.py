@@ -601,9 +601,10 @@ def hall(args, g, torch):
     disordered Haldane model: honeycomb 512 x 512 cells (N = 524,288), t1 = -1,
     t2 = 0.15, phi = pi/2, Anderson W = 1, one random-phase vector, M = 1024
     Kubo-Bastin moments, sigma_xy on 2001 energies.  Times gqt_kb_moments (the
-    two chains plus the M x M complex contraction) with the FP64 contraction and
-    with the split-TF32 tensor-core contraction, and gqt_kubo_bastin, with CUDA
-    events; per-kernel times from the library's profiler (families 7-9)."""
+    two chains plus the M x M complex contraction) in three forms -- FP32 storage
+    with the split-TF32 tensor-core contraction, FP64 chains with it, and FP64
+    throughout -- and gqt_kubo_bastin, with CUDA events; per-kernel times from the
+    library's profiler (families 7-9)."""
     L = args.hall_L or (32 if args.small else 512)
     M = args.hall_moments or (128 if args.small else 1024)
     seed = 1705013875
@@ -622,21 +623,24 @@ def hall(args, g, torch):
            "metric": "Kubo-Bastin orbital-moment pairs/s (N R M^2 / time of gqt_kb_moments)",
            "energies": int(E.numel()), "modes": {}}
     sigmas = {}
-    for mode, name in ((1, "tensor_core_split_tf32"), (0, "fp64")):
+    ham32 = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP32_ACC64)
+    r32 = r.to(torch.complex64)
+    for mode, name in ((2, "fp32_chains_tensor_core"), (1, "tensor_core_split_tf32"), (0, "fp64")):
         if mode == 0 and args.hall_skip_fp64:
             continue
-        g.gqt_set_kb_contraction(ham, mode)
+        h_, r_ = (ham32, r32) if mode == 2 else (ham, r)
+        g.gqt_set_kb_contraction(h_, min(mode, 1))
         lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
         sig = torch.empty_like(E)
         for _ in range(max(1, args.warmup)):
-            g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+            g.gqt_kb_moments(h_, r_, 1, M, 0, 1, lam)
             g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         g.gqt_profile_start()
         ev[0].record()
         for _ in range(steps):
-            g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+            g.gqt_kb_moments(h_, r_, 1, M, 0, 1, lam)
         ev[1].record()
         for _ in range(steps):
             g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
@@ -667,9 +671,11 @@ def hall(args, g, torch):
                         "k_kb_step_launches": int(prof_n[7]) // steps, "contraction_ms": gemm_s * 1e3,
                         "k_kb_integrand_ms": prof_ms[9] / max(int(prof_n[9]), 1)},
             "roofline": roof, "sigma_xy_gap_centre_e2_over_h": float(s_np[i0])}
-    if 0 in sigmas and 1 in sigmas:
-        out["sigma_xy_max_abs_diff_tc_vs_fp64"] = float(np.max(np.abs(sigmas[1] - sigmas[0])))
-    first = out["modes"].get("tensor_core_split_tf32") or out["modes"]["fp64"]
+    if 0 in sigmas:
+        for mode, key in ((1, "tensor_core_split_tf32"), (2, "fp32_chains_tensor_core")):
+            if mode in sigmas:
+                out["modes"][key]["sigma_xy_max_abs_diff_vs_fp64"] = float(np.max(np.abs(sigmas[mode] - sigmas[0])))
+    first = out["modes"]["fp32_chains_tensor_core"]
     out["value"] = first["value"]
     if not args.no_cpu_baseline:
         import oracle as O  # the CPU baseline leg only

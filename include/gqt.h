@@ -215,8 +215,10 @@ gqt_status gqt_bond_gradients(const double* d_g_slot, long long n_slots, const l
  * (d = bond_dx for 0, bond_dy for 1: (v~ x)_i = i sum_k d_ik H~_ik x_j),
  * estimated from R unit-norm vectors d_r [n][R] (FP64 complex, site-major) as
  * (N/R) sum_r <T_m v~_a r | v~_b T_n r>.  d_lambda: device FP64 complex
- * [M][M] (row m, interleaved re, im).  FP64 handles with one segment only;
- * direction 1 needs a lattice with bond_dy.  Workspace of the handle:
+ * [M][M] (row m, interleaved re, im).  One segment only; direction 1 needs a
+ * lattice with bond_dy.  FP64 handles take d_r complex128; FP32 handles
+ * (GQT_FP32_ACC64) take complex64, run the chains in FP32 and need the
+ * tensor-core contraction (gqt_set_kb_contraction(ham, 1)), else GQT_EINVAL.  Workspace of the handle:
  * 2 M N R + 3 N R complex vectors (the stacks T_m v~_a r and v~_b T_n r) plus
  * the split partial sums.  Synchronises the stream before returning. */
 gqt_status gqt_kb_moments(gqt_ham* ham, const void* d_r, int R, int M, int alpha, int beta, double* d_lambda,

@@ -42,14 +42,18 @@ namespace {
 
 enum { WS_HALL_P = 40, WS_HALL_B, WS_HALL_Q, WS_HALL_PART, WS_HALL_F, WS_HALL_W };
 
-template <bool CH>
+// H~ of a handle in the chain kernels: FP64 (double, double2 vectors) or FP32
+// storage (float, float2 vectors; the tensor-core contraction only).
+template <bool F64, bool CH>
 struct HallEll {
-  using HT = typename std::conditional<CH, double2, double>::type;
+  using S = typename std::conditional<F64, double, float>::type;
+  using V = typename std::conditional<F64, double2, float2>::type;
+  using HT = typename std::conditional<CH, V, S>::type;
   int64_t n;
   int K;
   const int* __restrict__ idx;  // slot-major [K][n]
   const HT* __restrict__ hop2;  // 2 H~ per slot
-  const double* __restrict__ diag2;
+  const S* __restrict__ diag2;
 };
 
 __device__ __forceinline__ double2 mla(double2 acc, double h, double2 x) {
@@ -64,13 +68,29 @@ __device__ __forceinline__ double2 mla(double2 acc, double2 h, double2 x) {
   acc.y = fma(h.y, x.x, acc.y);
   return acc;
 }
+__device__ __forceinline__ float2 mla(float2 acc, float h, float2 x) {
+  acc.x = fmaf(h, x.x, acc.x);
+  acc.y = fmaf(h, x.y, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 mla(float2 acc, float2 h, float2 x) {
+  acc.x = fmaf(h.x, x.x, acc.x);
+  acc.x = fmaf(-h.y, x.y, acc.x);
+  acc.y = fmaf(h.x, x.y, acc.y);
+  acc.y = fmaf(h.y, x.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 mk(double2, double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mk(float2, float x, float y) { return make_float2(x, y); }
 
-// Split of an FP64 value into two TF32 numbers (FP32 with the low 13 mantissa
-// bits zero, as the tensor cores read them): f = x rounded to FP32, hi = f rounded
-// to TF32, lo = f - hi (exact in FP32; the tensor cores keep its top 11 bits).
-// hi + lo carries about 22 significant bits; the FP32 rounding of x (2^-24) is
-// below that, and forming lo from f keeps the split to one FP64-pipe conversion.
-__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+// Split of a value into two TF32 numbers (FP32 with the low 13 mantissa bits
+// zero, as the tensor cores read them): f = x rounded to FP32, hi = f rounded to
+// TF32, lo = f - hi (exact in FP32; the tensor cores keep its top 11 bits).
+// hi + lo carries about 22 significant bits; the FP32 rounding of an FP64 x
+// (2^-24) is below that, and forming lo from f keeps the split to one FP64-pipe
+// conversion.
+template <class T>
+__device__ __forceinline__ void split_tf32(T x, float& hi, float& lo) {
   const float f = (float)x;
   hi = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
   lo = f - hi;
@@ -79,7 +99,8 @@ __device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
 struct TcPlanes {
   float *re_hi, *im_hi, *re_lo, *im_lo;
 };
-__device__ __forceinline__ void store_split(const TcPlanes& t, size_t e, double2 v) {
+template <class V>
+__device__ __forceinline__ void store_split(const TcPlanes& t, size_t e, V v) {
   float h, l;
   split_tf32(v.x, h, l);
   t.re_hi[e] = h;
@@ -89,21 +110,26 @@ __device__ __forceinline__ void store_split(const TcPlanes& t, size_t e, double2
   t.im_lo[e] = l;
 }
 
-// y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2); with
-// yhi/ylo also its TF32 split (the tensor-core contraction's operands).
-template <bool CH>
-__global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R, size_t total,
-                              const double2* __restrict__ x, double2* __restrict__ y, TcPlanes ys) {
+// y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2); with ys
+// also its TF32 split (the tensor-core contraction's operands).  D: the type of
+// the displacements (FP32 handles keep dx in FP32, dy always in FP64).
+template <bool F64, bool CH, class D>
+__global__ void k_kb_velocity(HallEll<F64, CH> H, const D* __restrict__ d, int R, size_t total,
+                              const typename HallEll<F64, CH>::V* __restrict__ x,
+                              typename HallEll<F64, CH>::V* __restrict__ y, TcPlanes ys) {
+  using V = typename HallEll<F64, CH>::V;
+  using S = typename HallEll<F64, CH>::S;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
-    double2 s = make_double2(0.0, 0.0);
+    V s = mk(V(), (S)0, (S)0);
     for (int k = 0; k < H.K; ++k) {
       const size_t sl = (size_t)k * H.n + i;
-      const double2 xj = x[(size_t)H.idx[sl] * R + r];
-      s = mla(s, H.hop2[sl], make_double2(d[sl] * xj.x, d[sl] * xj.y));
+      const V xj = x[(size_t)H.idx[sl] * R + r];
+      const S dd = (S)d[sl];
+      s = mla(s, H.hop2[sl], mk(V(), dd * xj.x, dd * xj.y));
     }
-    const double2 v = make_double2(-0.5 * s.y, 0.5 * s.x);
+    const V v = mk(V(), (S)-0.5 * s.y, (S)0.5 * s.x);
     y[e] = v;
     if (ys.re_hi) store_split(ys, e, v);
   }
@@ -111,15 +137,18 @@ __global__ void k_kb_velocity(HallEll<CH> H, const double* __restrict__ d, int R
 
 // Velocity hoppings vh_s = d_s * hop2_s of direction b (slot-major like hop2), so
 // that the velocity in k_kb_step costs one multiply-add per slot.
-template <bool CH>
-__global__ void k_kb_vhop(HallEll<CH> H, const double* __restrict__ d, typename HallEll<CH>::HT* __restrict__ vh) {
+template <bool F64, bool CH, class D>
+__global__ void k_kb_vhop(HallEll<F64, CH> H, const D* __restrict__ d, typename HallEll<F64, CH>::HT* __restrict__ vh) {
+  using S = typename HallEll<F64, CH>::S;
+  using V = typename HallEll<F64, CH>::V;
   const size_t total = (size_t)H.K * H.n;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const auto h = H.hop2[t];
+    const S dd = (S)d[t];
     if constexpr (CH)
-      vh[t] = make_double2(d[t] * h.x, d[t] * h.y);
+      vh[t] = mk(V(), dd * h.x, dd * h.y);
     else
-      vh[t] = d[t] * h;
+      vh[t] = dd * h;
   }
 }
 
@@ -129,42 +158,47 @@ __global__ void k_kb_vhop(HallEll<CH> H, const double* __restrict__ d, typename 
 //   B_k = v~_b Q_k                (from the same gathers of Q_k; vh = d_b * hop2)
 // TC: P_{k+1} and B_k also (or, for B_k, only) go to the planar TF32-split stacks
 // (ps: entry k+1, bs: entry k); bout may then be null.
-template <bool CH>
-__global__ void __launch_bounds__(256) k_kb_step(HallEll<CH> H, const typename HallEll<CH>::HT* __restrict__ vh,
-                                                 int R, size_t total,
-                                                 const double2* __restrict__ pk, const double2* __restrict__ pkm1,
-                                                 double2* __restrict__ pout, const double2* __restrict__ qk,
-                                                 const double2* __restrict__ qkm1, double2* __restrict__ qout,
-                                                 double2* __restrict__ bout, int first, int last, TcPlanes ps,
-                                                 TcPlanes bs) {
+template <bool F64, bool CH>
+__global__ void __launch_bounds__(256) k_kb_step(HallEll<F64, CH> H,
+                                                 const typename HallEll<F64, CH>::HT* __restrict__ vh, int R,
+                                                 size_t total, const typename HallEll<F64, CH>::V* __restrict__ pk,
+                                                 const typename HallEll<F64, CH>::V* __restrict__ pkm1,
+                                                 typename HallEll<F64, CH>::V* __restrict__ pout,
+                                                 const typename HallEll<F64, CH>::V* __restrict__ qk,
+                                                 const typename HallEll<F64, CH>::V* __restrict__ qkm1,
+                                                 typename HallEll<F64, CH>::V* __restrict__ qout,
+                                                 typename HallEll<F64, CH>::V* __restrict__ bout, int first, int last,
+                                                 TcPlanes ps, TcPlanes bs) {
+  using V = typename HallEll<F64, CH>::V;
+  using S = typename HallEll<F64, CH>::S;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
-    const double dg = H.diag2[i];
-    double2 a = make_double2(0.0, 0.0), q = a, b = a;
+    const S dg = H.diag2[i];
+    V a = mk(V(), (S)0, (S)0), q = a, b = a;
     for (int k = 0; k < H.K; ++k) {
       const size_t sl = (size_t)k * H.n + i;
       const size_t j = (size_t)H.idx[sl] * R + r;
       const auto h2 = H.hop2[sl];
-      const double2 qj = qk[j];
+      const V qj = qk[j];
       q = mla(q, h2, qj);
       b = mla(b, vh[sl], qj);
       if (!last) a = mla(a, h2, pk[j]);
     }
-    const double2 bv = make_double2(-0.5 * b.y, 0.5 * b.x);
+    const V bv = mk(V(), (S)-0.5 * b.y, (S)0.5 * b.x);
     if (bout) bout[e] = bv;
     if (bs.re_hi) store_split(bs, e, bv);
     if (last) continue;
     a = mla(a, dg, pk[e]);
     q = mla(q, dg, qk[e]);
-    double2 pn;
+    V pn;
     if (first) {
-      pn = make_double2(0.5 * a.x, 0.5 * a.y);
-      qout[e] = make_double2(0.5 * q.x, 0.5 * q.y);
+      pn = mk(V(), (S)0.5 * a.x, (S)0.5 * a.y);
+      qout[e] = mk(V(), (S)0.5 * q.x, (S)0.5 * q.y);
     } else {
-      const double2 p0 = pkm1[e], q0 = qkm1[e];
-      pn = make_double2(a.x - p0.x, a.y - p0.y);
-      qout[e] = make_double2(q.x - q0.x, q.y - q0.y);
+      const V p0 = pkm1[e], q0 = qkm1[e];
+      pn = mk(V(), a.x - p0.x, a.y - p0.y);
+      qout[e] = mk(V(), q.x - q0.x, q.y - q0.y);
     }
     pout[e] = pn;
     if (ps.re_hi) store_split(ps, e, pn);
@@ -553,38 +587,44 @@ int grid_for(size_t total) {
   return (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)gqt::sm_count() * 8));
 }
 
-template <bool CH>
-void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* da, const double* db, double2* lam,
+// F64: the handle's storage precision (FP32 handles run the chains in FP32 and
+// use the tensor-core contraction); DA, DB: the types of the two directions'
+// displacements.
+template <bool F64, bool CH, class DA, class DB>
+void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, const DB* db, double2* lam,
                      cudaStream_t st) {
-  HallEll<CH> H;
+  using HE = HallEll<F64, CH>;
+  using V = typename HE::V;
+  HE H;
   H.n = h->n;
   H.K = h->K;
   H.idx = (const int*)h->d_idx.p;
-  H.hop2 = (const typename HallEll<CH>::HT*)h->d_hop.p;
-  H.diag2 = (const double*)h->d_diag.p;
+  H.hop2 = (const typename HE::HT*)h->d_hop.p;
+  H.diag2 = (const typename HE::S*)h->d_diag.p;
+  const V* r = (const V*)rv;
   const bool tc = h->kb_mode == 1;
   const size_t total = (size_t)h->n * R;
-  const size_t vb = total * sizeof(double2);
+  const size_t vb = total * sizeof(V);
   const int g = grid_for(total);
-  double2* Q = (double2*)h->ws(WS_HALL_Q, vb * 3).p;
-  auto qbuf = [&](int k) -> double2* { return Q + (size_t)(k % 3) * total; };
+  V* Q = (V*)h->ws(WS_HALL_Q, vb * 3).p;
+  auto qbuf = [&](int k) -> V* { return Q + (size_t)(k % 3) * total; };
   const size_t mm = (size_t)M * M;
-  using HT = typename HallEll<CH>::HT;
+  using HT = typename HE::HT;
   HT* vh = (HT*)h->ws(WS_HALL_W, (size_t)H.K * H.n * sizeof(HT)).p;
-  k_kb_vhop<CH><<<grid_for((size_t)H.K * H.n), 256, 0, st>>>(H, db, vh);
+  k_kb_vhop<F64, CH, DB><<<grid_for((size_t)H.K * H.n), 256, 0, st>>>(H, db, vh);
   check_launch("k_kb_vhop");
-  if (!tc) {
+  if constexpr (F64) if (!tc) {
     double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
     double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
     const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
-    k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, none);
+    k_kb_velocity<F64, CH, DA><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, none);
     check_launch("k_kb_velocity");
     for (int k = 0; k < M; ++k) {
       const bool last = k == M - 1;
-      const double2* qk = k == 0 ? r : qbuf(k);
-      const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
+      const V* qk = k == 0 ? r : qbuf(k);
+      const V* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
       const size_t pe = prof_begin(st);
-      k_kb_step<CH><<<g, 256, 0, st>>>(H, vh, R, total, Pst + (size_t)k * total,
+      k_kb_step<F64, CH><<<g, 256, 0, st>>>(H, vh, R, total, Pst + (size_t)k * total,
                                         k == 0 ? nullptr : Pst + (size_t)(k - 1) * total,
                                         last ? nullptr : Pst + (size_t)(k + 1) * total, qk, qkm1,
                                         last ? nullptr : qbuf(k + 1), Bst + (size_t)k * total, k == 0, last, none,
@@ -610,9 +650,10 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     check_launch("k_kb_reduce");
     return;
   }
-  // tensor-core contraction: chains in FP64 (rolling buffers), stacks in planar split TF32
-  double2* Pr = (double2*)h->ws(WS_HALL_P, vb * 3).p;
-  auto pbuf = [&](int k) -> double2* { return Pr + (size_t)(k % 3) * total; };
+  // tensor-core contraction: chains in the handle's precision (rolling buffers),
+  // stacks in planar split TF32
+  V* Pr = (V*)h->ws(WS_HALL_P, vb * 3).p;
+  auto pbuf = [&](int k) -> V* { return Pr + (size_t)(k % 3) * total; };
   const size_t ld = (total + 3) / 4 * 4;
   const size_t plane = (size_t)M * ld;
   float* pl = (float*)h->ws(WS_HALL_B, plane * 8 * sizeof(float)).p;
@@ -627,14 +668,14 @@ void kb_moments_impl(gqt_ham* h, const double2* r, int R, int M, const double* d
     return t;
   };
   const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
-  k_kb_velocity<CH><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), planes(0, 0));
+  k_kb_velocity<F64, CH, DA><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), planes(0, 0));
   check_launch("k_kb_velocity");
   for (int k = 0; k < M; ++k) {
     const bool last = k == M - 1;
-    const double2* qk = k == 0 ? r : qbuf(k);
-    const double2* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
+    const V* qk = k == 0 ? r : qbuf(k);
+    const V* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
     const size_t pe = prof_begin(st);
-    k_kb_step<CH><<<g, 256, 0, st>>>(H, vh, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
+    k_kb_step<F64, CH><<<g, 256, 0, st>>>(H, vh, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
                                       last ? nullptr : pbuf(k + 1), qk, qkm1, last ? nullptr : qbuf(k + 1), nullptr,
                                       k == 0, last, last ? none : planes(0, k + 1), planes(4, k));
     check_launch("k_kb_step");
@@ -673,17 +714,37 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
   try {
     if (!h || !d_r || !d_lambda || R < 1 || M < 1 || alpha < 0 || alpha > 1 || beta < 0 || beta > 1)
       throw Error(GQT_EINVAL, "gqt_kb_moments: bad argument");
-    if (h->prec != GQT_FP64) throw Error(GQT_EINVAL, "gqt_kb_moments: needs an FP64 handle");
+    if (h->prec != GQT_FP64 && h->kb_mode != 1)
+      throw Error(GQT_EINVAL, "gqt_kb_moments: an FP32 handle needs the tensor-core contraction "
+                              "(gqt_set_kb_contraction(ham, 1))");
     if (h->nseg != 1) throw Error(GQT_EINVAL, "gqt_kb_moments: one segment only");
     if ((alpha == 1 || beta == 1) && !h->has_dy)
       throw Error(GQT_EINVAL, "gqt_kb_moments: the lattice has no y displacements (bond_dy)");
     check_cuda(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
-    const double* d[2] = {(const double*)h->d_dx.p, (const double*)h->d_dy.p};
-    if (h->hop_real)
-      kb_moments_impl<false>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
-    else
-      kb_moments_impl<true>(h, (const double2*)d_r, R, M, d[alpha], d[beta], (double2*)d_lambda, st);
+    double2* lam = (double2*)d_lambda;
+    if (h->prec == GQT_FP64) {
+      const double* d[2] = {(const double*)h->d_dx.p, (const double*)h->d_dy.p};
+      if (h->hop_real)
+        kb_moments_impl<true, false>(h, d_r, R, M, d[alpha], d[beta], lam, st);
+      else
+        kb_moments_impl<true, true>(h, d_r, R, M, d[alpha], d[beta], lam, st);
+    } else {
+      // FP32 storage: dx is FP32, dy FP64
+      const float* dxf = (const float*)h->d_dx.p;
+      const double* dyd = (const double*)h->d_dy.p;
+      auto run = [&](auto ch) {
+        constexpr bool CH = decltype(ch)::value;
+        if (alpha == 0 && beta == 0) kb_moments_impl<false, CH>(h, d_r, R, M, dxf, dxf, lam, st);
+        if (alpha == 0 && beta == 1) kb_moments_impl<false, CH>(h, d_r, R, M, dxf, dyd, lam, st);
+        if (alpha == 1 && beta == 0) kb_moments_impl<false, CH>(h, d_r, R, M, dyd, dxf, lam, st);
+        if (alpha == 1 && beta == 1) kb_moments_impl<false, CH>(h, d_r, R, M, dyd, dyd, lam, st);
+      };
+      if (h->hop_real)
+        run(std::integral_constant<bool, false>());
+      else
+        run(std::integral_constant<bool, true>());
+    }
     int flag = 0;
     if (h->kb_mode == 1)
       check_cuda(cudaMemcpyAsync(&flag, h->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");

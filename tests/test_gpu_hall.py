@@ -223,3 +223,44 @@ def test_haldane_plateau_finite_temperature():
         out[kT] = sig.cpu().numpy()
     assert abs(out[0.02][0] - 1.0) < 1e-2 and abs(out[0.0][0] - 1.0) < 1e-2
     assert abs(out[0.3][1] - out[0.0][1]) > 1e-3
+
+
+def _gpu_lambda_fp32(lat, dE, ph, M, a, b):
+    ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP32_ACC64)
+    g.gqt_set_kb_contraction(ham, 1)
+    lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+    g.gqt_kb_moments(ham, torch.from_numpy(ph).to(torch.complex64).cuda(), ph.shape[1], M, a, b, lam)
+    return lam
+
+
+@pytest.mark.parametrize("name", ["haldane", "square_phases", "honeycomb_real"])
+@pytest.mark.parametrize("M,R", [(17, 1), (70, 2), (130, 1)])
+@pytest.mark.parametrize("pair", ["xy", "xx"])
+def test_kb_moments_fp32_chains(name, M, R, pair):
+    """FP32 storage (H~ and the chains in FP32) with the tensor-core contraction:
+    within 1e-5 of the oracle run on the same (FP32-rounded) vectors (measured up
+    to 2.4e-6: the chains' FP32 rounding is below the contraction's)."""
+    lat, dE = _model(name)
+    ph = S.random_phase(lat.n, R, seed=34).astype(np.complex64).astype(np.complex128)
+    d = {"x": (0, lat.dx), "y": (1, lat.dy)}
+    (a, da), (b, db) = d[pair[0]], d[pair[1]]
+    got = _gpu_lambda_fp32(lat, dE, ph, M, a, b).cpu().numpy()
+    ref = O.Hamiltonian(lat, dE).kb_moments(da, db, ph, M)
+    err = nerr(got, ref)
+    assert err < 1e-5, err
+
+
+def test_haldane_chern_plateau_fp32_chains():
+    lat = S.haldane(8, 8, -1.0, 0.15, math.pi / 2, 0.0, 0.0)
+    dE = 1.05 * (3.0 + 6 * 0.15)
+    basis = np.eye(lat.n, dtype=np.complex128)
+    M = 256
+    E = torch.from_numpy(np.linspace(-0.97 * dE, 0.0, 3001)).cuda()
+    out = {}
+    for name, lam in (("fp32", _gpu_lambda_fp32(lat, dE, basis, M, 0, 1)), ("fp64", _gpu_lambda(lat, dE, basis, M, 0, 1))):
+        sig = torch.empty(E.numel(), dtype=torch.float64, device="cuda")
+        g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
+        out[name] = sig.cpu().numpy()
+    assert abs(out["fp32"][-1] - 1.0) < 1e-2
+    diff = float(np.max(np.abs(out["fp32"] - out["fp64"])))
+    assert diff < 1e-4, diff  # measured 1.4e-5
