@@ -657,7 +657,8 @@ def hall(args, g, torch):
                     "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)"}
         else:
             macs = 3.0 * 2 * M * M * (2.0 * n)  # three split products, Re and Im, 2N real terms
-            roof = {"kernel": "k_kb_gemm_tc (tcgen05 kind::tf32, three split products)", "bound": "tensor",
+            roof = {"kernel": "k_kb_gemm_tma (TMA-fed tcgen05 kind::tf32, 128 x 256 tiles, three split products)",
+                    "bound": "tensor",
                     "achieved": 2 * macs / gemm_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s (TF32)",
                     "frac": 2 * macs / gemm_s / 1e12 / tf32_peak,
                     "peak_source": "measured BF16 GEMM (MEASURED_PEAKS.json bf16_tflops) x nominal TF32/BF16 1.1/2.25"}

@@ -19,6 +19,8 @@
 // split over the contraction.  k_kb_integrand evaluates the double sum on an
 // energy grid (a bilinear form per energy), and k_kb_scan integrates it.
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <math_constants.h>
@@ -95,19 +97,25 @@ __device__ __forceinline__ void split_tf32(T x, float& hi, float& lo) {
   hi = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
   lo = f - hi;
 }
-// Planar TF32-split stack entry: re_hi, im_hi, re_lo, im_lo planes (null re_hi: none).
+// TF32-split stack entry (row m of the re_hi, im_hi, re_lo, im_lo planes; null
+// re_hi: none).  A plane is blocked by 8 contraction sites, [chunk][row][8], so
+// that an operand tile of the tensor-core contraction (8 sites of 128 rows) is
+// one contiguous 4 KB block: the pointers address row m of chunk 0, cs is the
+// chunk stride (M * 8 floats).
 struct TcPlanes {
   float *re_hi, *im_hi, *re_lo, *im_lo;
+  size_t cs;
 };
 template <class V>
 __device__ __forceinline__ void store_split(const TcPlanes& t, size_t e, V v) {
+  const size_t o = (e >> 3) * t.cs + (e & 7);
   float h, l;
   split_tf32(v.x, h, l);
-  t.re_hi[e] = h;
-  t.re_lo[e] = l;
+  t.re_hi[o] = h;
+  t.re_lo[o] = l;
   split_tf32(v.y, h, l);
-  t.im_hi[e] = h;
-  t.im_lo[e] = l;
+  t.im_hi[o] = h;
+  t.im_lo[o] = l;
 }
 
 // y = v~ x = i sum_s d_s H~_s x_j (hop2 = 2 H~, so the factor is i/2); with ys
@@ -268,42 +276,13 @@ __global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ 
 // The same contraction on the tcgen05 tensor cores in split TF32 (three products
 // hi*hi + hi*lo + lo*hi per pair, FP32 accumulation in tensor memory over one
 // split of the contraction, splits summed in FP64).  The stacks are planar
-// (real and imaginary planes [M][ld], ld = N R rounded up to 4), so with
+// (real and imaginary planes, blocked by 8 sites as described at TcPlanes), so
+// with
 //   Re Lambda = Pre.Bre + Pim.Bim,  Im Lambda = Pre.Bim - Pim.Bre
-// every operand is a plain tile of a plane.  One CTA of 256 threads computes a
-// 128 x 128 output tile into three accumulators of 128 tensor-memory columns
-// (Re, Pre.Bim, Pim.Bre); contraction stages of 16 sites pass through three
-// shared-memory buffers filled by cp.async two stages ahead of the products.
-// Operands are K-major without swizzle: core matrices of 8 rows x 16 B,
-// K-adjacent ones TC_LBO bytes apart (144, so a row's chunks land in distinct
-// banks), 8-row groups TC_SBO bytes apart.
-constexpr int TC_TM = 128, TC_TK = 16, TC_LBO = 144, TC_SBO = 4 * TC_LBO, TC_TILE = 16 * TC_SBO;
-constexpr int TC_NT = 8;                      // Pre hi/lo, Pim hi/lo, Bre hi/lo, Bim hi/lo
-constexpr int TC_STAGE = TC_NT * TC_TILE;     // 73,728 B
-constexpr int TC_NBUF = 3;
-constexpr int TC_SMEM = TC_NBUF * TC_STAGE + 64;
+// every operand is a plain tile of a plane.
 constexpr int TC_WAIT_LIMIT = 1 << 24;
-constexpr int TC_THREADS = 256;  // 8 warps issue the copies; thread 0 the products
-
-struct TcOperands {
-  const float* plane[TC_NT];  // same order as the shared-memory tiles
-};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  // kind::tf32, D f32, A and B K-major, M = 128, N = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
 // Bounded wait for the completion of phase `parity` of an mbarrier; false on timeout.
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
@@ -328,124 +307,183 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// One stage of copies: 8 tiles x 128 rows x 4 chunks of 16 B, two per thread
-// per tile (256 threads); rows past M and sites past ke are filled with zeros
-// (source size 0).
-__device__ __forceinline__ void tc_fill(const TcOperands& op, unsigned char* st, int m0, int n0, int M, size_t ld,
-                                        size_t k0, size_t ke) {
-#pragma unroll
-  for (int t = 0; t < TC_NT; ++t) {
-    const int base = t < 4 ? m0 : n0;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = threadIdx.x + TC_THREADS * q;
-      const int row = idx >> 2, kq = idx & 3;
-      const size_t k = k0 + 4 * kq;
-      const bool valid = base + row < M && k < ke;
-      const float* src = valid ? op.plane[t] + (size_t)(base + row) * ld + k : op.plane[t];
-      const uint32_t dst = smem_addr(st + t * TC_TILE + (row >> 3) * TC_SBO + kq * TC_LBO + (row & 7) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0));
-    }
-  }
+// Wide tiles fed by TMA: one CTA computes a 128 x 256 output tile into two
+// accumulators of 256 tensor-memory columns (Re, Im).  The instruction
+// descriptor's negate-A bit gives Im = Pre.Bim - Pim.Bre in one accumulator, so
+// each 8-site stage is 12 products of 128 x 256 x 8 from 4 A tiles of 128 rows
+// and 4 B tiles of 256 rows (48 KB): a third fewer operand bytes per product
+// than a 128 x 128 tile.  One thread drives the pipeline: a 4-D tensor map over
+// the blocked planes (site within chunk, row, chunk, plane) brings each tile in
+// as bulk tensor copies of contiguous 4 KB blocks (32-B rows, 32-B swizzle; rows
+// past M read as zeros) that complete on the stage's mbarrier, the products of
+// a stage go out as soon as it has landed,
+// and a buffer is refilled, NBUF - 1 stages ahead, once the products that read
+// it have completed.  Every wait is bounded; after a timeout the thread drains
+// what is still in flight (again bounded) and the kernel reports it.
+constexpr int TM_TM = 128, TM_TN = 256, TM_TK = 8;       // 8 FP32 sites: one 32-B swizzle span per row
+constexpr int TM_ATILE = TM_TM * 32, TM_BTILE = TM_TN * 32;  // 4 KB, 8 KB
+constexpr int TM_BOX = 128 * 32;                            // one copy: 8 sites x 128 rows
+constexpr int TM_STAGE = 4 * TM_ATILE + 4 * TM_BTILE;       // 48 KB
+constexpr int TM_NBUF = 4;
+constexpr int TM_SMEM = TM_NBUF * TM_STAGE + 1024 + 128;    // + 1 KB alignment slack, barriers
+constexpr int TM_THREADS = 256;
+
+// K-major operand, 32-B swizzle: rows of 32 B, 8-row groups 256 B apart.
+__device__ __forceinline__ uint64_t tm_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_kb_gemm_tc(TcOperands op, int M, size_t ld, size_t kchunk,
-                                                       double2* __restrict__ part, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char tc_sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tc_sm + TC_NBUF * TC_STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_sm + TC_NBUF * TC_STAGE + 32);
+// kind::tf32, D f32, A and B K-major, M = 128, N = 256; NEG: negate A (bit 13).
+template <bool NEG>
+__device__ __forceinline__ void tm_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (NEG ? (1u << 13) : 0u) |
+                             ((uint32_t)(TM_TN >> 3) << 17) | ((uint32_t)(TM_TM >> 4) << 24);
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Box of 8 sites x 128 rows at (row y, chunk c, plane z).
+__device__ __forceinline__ void tm_load(uint32_t dst, const CUtensorMap* map, int y, int c, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(c), "r"(z), "r"(bar)
+      : "memory");
+}
+
+struct TmPlanes {
+  int a[4];  // plane (z coordinate) of Pre_hi, Pre_lo, Pim_hi, Pim_lo
+  int b[4];  // Bre_hi, Bre_lo, Bim_hi, Bim_lo
+};
+
+__global__ void __launch_bounds__(TM_THREADS, 1) k_kb_gemm_tma(const __grid_constant__ CUtensorMap map, TmPlanes pz,
+                                                        int M, size_t kt, size_t kchunk, double2* __restrict__ part,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tm_raw[];
+  const uint32_t raw = smem_addr(tm_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzled tiles start on 1 KB
+  unsigned char* sm = tm_raw + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + TM_NBUF * TM_STAGE);
+  uint64_t* done = full + TM_NBUF;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + TM_NBUF);
+  int* okp = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int m0 = blockIdx.x * TC_TM, n0 = blockIdx.y * TC_TM;
+  const int m0 = blockIdx.x * TM_TM, n0 = blockIdx.y * TM_TN;
   const size_t kb = (size_t)blockIdx.z * kchunk;
-  const size_t ke = (kb + kchunk < ld) ? kb + kchunk : ld;
+  const size_t ke = (kb + kchunk < kt) ? kb + kchunk : kt;
+  const int nst = (int)((ke - kb + TM_TK - 1) / TM_TK);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int b = 0; b < TC_NBUF; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[b])), "r"(1));
+    for (int b = 0; b < TM_NBUF; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[b])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&done[b])), "r"(1));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
+    *okp = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  const int nst = (int)((ke - kb + TC_TK - 1) / TC_TK);
-  // prologue: stages 0 and 1 in flight (a group is committed for every stage index,
-  // empty past the end, so that wait_group counts stay uniform)
-  for (int s = 0; s < 2; ++s) {
-    if (s < nst) tc_fill(op, tc_sm + s * TC_STAGE, m0, n0, M, ld, kb + (size_t)s * TC_TK, ke);
-    asm volatile("cp.async.commit_group;");
-  }
-  bool ok = true;
-  for (int s = 0; s < nst; ++s) {
-    const int buf = s % TC_NBUF;
-    asm volatile("cp.async.wait_group 1;");
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t base = smem_addr(tc_sm + buf * TC_STAGE);
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+    auto issue = [&](int s) {
+      const int b = s % TM_NBUF;
+      const uint32_t st = base + b * TM_STAGE, fb = smem_addr(&full[b]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TM_STAGE) : "memory");
+      const int c = (int)(kb / TM_TK) + s;
 #pragma unroll
-      for (int j = 0; j < TC_TK / 8; ++j) {
-        const uint32_t o = (uint32_t)(j * 2 * TC_LBO);
-        uint64_t d[TC_NT];
+      for (int t = 0; t < 4; ++t) tm_load(st + t * TM_ATILE, &map, m0, c, pz.a[t], fb);
 #pragma unroll
-        for (int t = 0; t < TC_NT; ++t) d[t] = tc_desc(base + t * TC_TILE + o);
-        // d: 0 Pre_hi, 1 Pre_lo, 2 Pim_hi, 3 Pim_lo, 4 Bre_hi, 5 Bre_lo, 6 Bim_hi, 7 Bim_lo
-        const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
-        tc_mma(tmem, d[0], d[4], acc);
-        tc_mma(tmem, d[0], d[5], 1u);
-        tc_mma(tmem, d[1], d[4], 1u);
-        tc_mma(tmem, d[2], d[6], 1u);
-        tc_mma(tmem, d[2], d[7], 1u);
-        tc_mma(tmem, d[3], d[6], 1u);
-        tc_mma(tmem + 128, d[0], d[6], acc);
-        tc_mma(tmem + 128, d[0], d[7], 1u);
-        tc_mma(tmem + 128, d[1], d[6], 1u);
-        tc_mma(tmem + 256, d[2], d[4], acc);
-        tc_mma(tmem + 256, d[2], d[5], 1u);
-        tc_mma(tmem + 256, d[3], d[4], 1u);
+      for (int t = 0; t < 4; ++t) {
+        const uint32_t bt = st + 4 * TM_ATILE + t * TM_BTILE;
+        tm_load(bt, &map, n0, c, pz.b[t], fb);
+        tm_load(bt + TM_BOX, &map, n0 + 128, c, pz.b[t], fb);
       }
+    };
+    int issued = 0, landed = 0, committed = 0;
+    bool ok = true;
+    for (; issued < nst && issued < TM_NBUF; ++issued) issue(issued);
+    for (int s = 0; s < nst; ++s) {
+      const int b = s % TM_NBUF;
+      if (!tc_wait(&full[b], (uint32_t)((s / TM_NBUF) & 1))) {
+        ok = false;
+        break;
+      }
+      landed = s + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t st = base + b * TM_STAGE;
+      uint64_t a[4], bb[4];  // a: Pre_hi, Pre_lo, Pim_hi, Pim_lo; bb: Bre_hi, Bre_lo, Bim_hi, Bim_lo
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        a[t] = tm_desc(st + t * TM_ATILE);
+        bb[t] = tm_desc(st + 4 * TM_ATILE + t * TM_BTILE);
+      }
+      const uint32_t acc = s > 0 ? 1u : 0u;
+      tm_mma<false>(tmem, a[0], bb[0], acc);  // Re = Pre.Bre + Pim.Bim
+      tm_mma<false>(tmem, a[0], bb[1], 1u);
+      tm_mma<false>(tmem, a[1], bb[0], 1u);
+      tm_mma<false>(tmem, a[2], bb[2], 1u);
+      tm_mma<false>(tmem, a[2], bb[3], 1u);
+      tm_mma<false>(tmem, a[3], bb[2], 1u);
+      tm_mma<false>(tmem + TM_TN, a[0], bb[2], acc);  // Im = Pre.Bim - Pim.Bre
+      tm_mma<false>(tmem + TM_TN, a[0], bb[3], 1u);
+      tm_mma<false>(tmem + TM_TN, a[1], bb[2], 1u);
+      tm_mma<true>(tmem + TM_TN, a[2], bb[0], 1u);
+      tm_mma<true>(tmem + TM_TN, a[2], bb[1], 1u);
+      tm_mma<true>(tmem + TM_TN, a[3], bb[0], 1u);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&bar[buf])));
+          smem_addr(&done[b])));
+      committed = s + 1;
+      // the products of stage s - 1 have read their buffer: refill it with stage
+      // s - 1 + NBUF while those of stage s run
+      if (s >= 1 && issued < nst) {
+        const int p = s - 1;
+        if (!tc_wait(&done[p % TM_NBUF], (uint32_t)((p / TM_NBUF) & 1))) {
+          ok = false;
+          break;
+        }
+        issue(issued++);
+      }
     }
-    // stage s + 2 reuses the buffer of stage s - 1: wait for its products
-    // (block-uniform outcome, so every thread takes the same path)
-    if (s >= 1 && !__syncthreads_and(tc_wait(&bar[(s - 1) % TC_NBUF], (uint32_t)(((s - 1) / TC_NBUF) & 1)))) {
+    // the last products (their completion implies that of all earlier ones); after
+    // a timeout also the copies still in flight
+    if (committed > 0 && !tc_wait(&done[(committed - 1) % TM_NBUF], (uint32_t)(((committed - 1) / TM_NBUF) & 1)))
       ok = false;
-      break;
+    if (!ok)
+      for (int s = landed; s < issued; ++s) tc_wait(&full[s % TM_NBUF], (uint32_t)((s / TM_NBUF) & 1));
+    if (!ok) {
+      *okp = 0;
+      atomicOr(err, 16);
     }
-    if (s + 2 < nst)
-      tc_fill(op, tc_sm + ((s + 2) % TC_NBUF) * TC_STAGE, m0, n0, M, ld, kb + (size_t)(s + 2) * TC_TK, ke);
-    asm volatile("cp.async.commit_group;");
   }
-  asm volatile("cp.async.wait_all;");
-  // the last stage's products (or, after a timeout, whatever is still in flight)
-  ok = __syncthreads_and(ok && (nst == 0 || tc_wait(&bar[(nst - 1) % TC_NBUF], (uint32_t)(((nst - 1) / TC_NBUF) & 1))));
-  if (!ok && tid == 0) atomicOr(err, 16);
+  __syncthreads();
+  const bool ok = *okp != 0;
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // warp w reads tensor-memory lanes 32 (w % 4) .. +31; warps 0-3 take columns
-    // 0..63, warps 4-7 columns 64..127
+    // 0..127, warps 4-7 columns 128..255
     const int quarter = warp & 3;
     const int m = m0 + quarter * 32 + (tid & 31);
     const uint32_t lane = (uint32_t)(quarter * 32) << 16;
-    const int cbeg = (warp >> 2) * (TC_TM / 2);
-    for (int c = cbeg; c < cbeg + TC_TM / 2; c += 32) {
-      uint32_t re[32], ia[32], ib[32];
+    const int cbeg = (warp >> 2) * (TM_TN / 2);
+    for (int c = cbeg; c < cbeg + TM_TN / 2; c += 32) {
+      uint32_t re[32], im[32];
       tc_ld32(tmem + lane + c, re);
-      tc_ld32(tmem + lane + 128 + c, ia);
-      tc_ld32(tmem + lane + 256 + c, ib);
+      tc_ld32(tmem + lane + TM_TN + c, im);
       if (m < M) {
         double2* dst = part + ((size_t)blockIdx.z * M + m) * M + n0 + c;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (n0 + c + j < M)
-            dst[j] = make_double2((double)__uint_as_float(re[j]),
-                                  (double)__uint_as_float(ia[j]) - (double)__uint_as_float(ib[j]));
+            dst[j] = make_double2((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
       }
     }
   }
@@ -577,6 +615,18 @@ __global__ void k_kb_fermi(const double* __restrict__ F, const double* __restric
   sigma[q] = pref * run;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (PFN_cuTensorMapEncodeTiled_v12000)p : nullptr;
+  }();
+  if (!fn) throw Error(GQT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  return fn;
+}
+
 double jackson_g(int n, int M) {
   const double a = 1.0 / (M + 1.0), pi = 3.14159265358979323846;
   return (1.0 - n * a) * std::cos(pi * n * a) + a * std::sin(pi * n * a) / std::tan(pi * a);
@@ -616,7 +666,7 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
   if constexpr (F64) if (!tc) {
     double2* Pst = (double2*)h->ws(WS_HALL_P, vb * M).p;
     double2* Bst = (double2*)h->ws(WS_HALL_B, vb * M).p;
-    const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
+    const TcPlanes none = {nullptr, nullptr, nullptr, nullptr, 0};
     k_kb_velocity<F64, CH, DA><<<g, 256, 0, st>>>(H, da, R, total, r, Pst, none);
     check_launch("k_kb_velocity");
     for (int k = 0; k < M; ++k) {
@@ -651,23 +701,32 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
     return;
   }
   // tensor-core contraction: chains in the handle's precision (rolling buffers),
-  // stacks in planar split TF32
+  // stacks in planar split TF32 blocked by 8 sites ([chunk][row][8] per plane,
+  // planes an odd number of 128-B lines apart)
   V* Pr = (V*)h->ws(WS_HALL_P, vb * 3).p;
   auto pbuf = [&](int k) -> V* { return Pr + (size_t)(k % 3) * total; };
-  const size_t ld = (total + 3) / 4 * 4;
-  const size_t plane = (size_t)M * ld;
+  const size_t nk = (total + TM_TK - 1) / TM_TK;  // chunks; the contraction runs over nk * 8 sites
+  if (nk > (size_t)INT32_MAX) throw Error(GQT_EINVAL, "gqt_kb_moments: N R too large");
+  const size_t cs = (size_t)M * TM_TK;             // chunk stride in floats
+  const size_t plane = [](size_t x) {
+    x = (x + 31) / 32 * 32;
+    return (x / 32) % 2 ? x : x + 32;
+  }(nk * cs);
   float* pl = (float*)h->ws(WS_HALL_B, plane * 8 * sizeof(float)).p;
-  if (ld != total) check_cuda(cudaMemsetAsync(pl, 0, plane * 8 * sizeof(float), st), "stack padding");
+  if (total % TM_TK)  // sites past N R in the last chunk: zeros
+    check_cuda(cudaMemset2DAsync(pl + (nk - 1) * cs, plane * sizeof(float), 0, cs * sizeof(float), 8, st),
+               "stack padding");
   // planes: P re_hi, im_hi, re_lo, im_lo (0..3); B the same (4..7)
   auto planes = [&](int first, size_t entry) {
     TcPlanes t;
-    t.re_hi = pl + (first + 0) * plane + entry * ld;
-    t.im_hi = pl + (first + 1) * plane + entry * ld;
-    t.re_lo = pl + (first + 2) * plane + entry * ld;
-    t.im_lo = pl + (first + 3) * plane + entry * ld;
+    t.re_hi = pl + (first + 0) * plane + entry * TM_TK;
+    t.im_hi = pl + (first + 1) * plane + entry * TM_TK;
+    t.re_lo = pl + (first + 2) * plane + entry * TM_TK;
+    t.im_lo = pl + (first + 3) * plane + entry * TM_TK;
+    t.cs = cs;
     return t;
   };
-  const TcPlanes none = {nullptr, nullptr, nullptr, nullptr};
+  const TcPlanes none = {nullptr, nullptr, nullptr, nullptr, 0};
   k_kb_velocity<F64, CH, DA><<<g, 256, 0, st>>>(H, da, R, total, r, pbuf(0), planes(0, 0));
   check_launch("k_kb_velocity");
   for (int k = 0; k < M; ++k) {
@@ -682,25 +741,46 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
     prof_end(pe, 7, st);
   }
   // splits: contraction chunks of about 8K sites (the FP32 accumulation span) and
-  // at least four waves of one CTA per SM
-  const int tiles = (M + TC_TM - 1) / TC_TM;
-  long long S = std::max<long long>((long long)((ld + 8191) / 8192),
-                                    (4LL * gqt::sm_count() + (long long)tiles * tiles - 1) / ((long long)tiles * tiles));
-  S = std::min<long long>(S, std::max<long long>(1, (long long)(ld / TC_TK)));
+  // at least four waves of one CTA per SM; among up to 1.5x that many splits the
+  // count whose last wave is fullest
+  const size_t kt = nk * TM_TK;
+  const int tm = (M + TM_TM - 1) / TM_TM, tn = (M + TM_TN - 1) / TM_TN;
+  const long long tiles = (long long)tm * tn, sms = gqt::sm_count();
+  long long S = std::max<long long>((long long)((kt + 8191) / 8192), (4 * sms + tiles - 1) / tiles);
+  {
+    long long best = S;
+    double best_cost = 1e300;
+    for (long long c = S; c <= S + S / 2; ++c) {
+      const double cost = (double)((tiles * c + sms - 1) / sms) / (double)c;
+      if (cost < best_cost * (1 - 1e-9)) best_cost = cost, best = c;
+    }
+    S = best;
+  }
+  S = std::min<long long>(S, (long long)nk);
   S = std::min<long long>(S, 65535);  // gridDim.z limit (longer splits beyond N R ~ 5e8)
-  const size_t kchunk = ((ld + S - 1) / S + TC_TK - 1) / TC_TK * TC_TK;
-  S = (long long)((ld + kchunk - 1) / kchunk);
+  const size_t kchunk = ((kt + S - 1) / S + TM_TK - 1) / TM_TK * TM_TK;
+  S = (long long)((kt + kchunk - 1) / kchunk);
   double2* part = (double2*)h->ws(WS_HALL_PART, (size_t)S * mm * sizeof(double2)).p;
-  TcOperands op;
-  const int order[TC_NT] = {0, 2, 1, 3, 4, 6, 5, 7};  // Pre_hi, Pre_lo, Pim_hi, Pim_lo, Bre_hi, Bre_lo, Bim_hi, Bim_lo
-  for (int t = 0; t < TC_NT; ++t) op.plane[t] = pl + order[t] * plane;
-  check_cuda(cudaFuncSetAttribute(k_kb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM),
-             "smem attribute");
+  // one 4-D tensor map over the eight planes: (site within chunk < 8, row < M,
+  // chunk < nk, plane < 8); boxes of 8 sites x 128 rows, 32-B swizzle
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)TM_TK, (cuuint64_t)M, (cuuint64_t)nk, 8};
+  const cuuint64_t strides[3] = {(cuuint64_t)(TM_TK * sizeof(float)), (cuuint64_t)(cs * sizeof(float)),
+                                 (cuuint64_t)(plane * sizeof(float))};
+  const cuuint32_t box[4] = {(cuuint32_t)TM_TK, 128, 1, 1}, estr[4] = {1, 1, 1, 1};
+  const CUresult cr = tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl, dims, strides, box, estr,
+                                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) throw Error(GQT_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)cr));
+  // plane of each operand tile: P re_hi 0, im_hi 1, re_lo 2, im_lo 3; B 4..7
+  const TmPlanes pz = {{0, 2, 1, 3}, {4, 6, 5, 7}};  // Pre_hi, Pre_lo, Pim_hi, Pim_lo; Bre_hi, Bre_lo, Bim_hi, Bim_lo
   check_cuda(cudaMemsetAsync(h->d_flag.p, 0, sizeof(int), st), "flag reset");
+  check_cuda(cudaFuncSetAttribute(k_kb_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TM_SMEM),
+             "smem attribute");
   const size_t pg = prof_begin(st);
-  k_kb_gemm_tc<<<dim3(tiles, tiles, (unsigned)S), TC_THREADS, TC_SMEM, st>>>(op, M, ld, kchunk, part,
-                                                                             (int*)h->d_flag.p);
-  check_launch("k_kb_gemm_tc");
+  k_kb_gemm_tma<<<dim3(tm, tn, (unsigned)S), TM_THREADS, TM_SMEM, st>>>(map, pz, M, kt, kchunk, part,
+                                                                        (int*)h->d_flag.p);
+  check_launch("k_kb_gemm_tma");
   prof_end(pg, 8, st);
   k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M, (double)h->n / R,
                                                                               lam);
@@ -746,7 +826,7 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
         run(std::integral_constant<bool, true>());
     }
     int flag = 0;
-    if (h->kb_mode == 1)
+    if (h->kb_mode != 0)
       check_cuda(cudaMemcpyAsync(&flag, h->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     check_cuda(cudaStreamSynchronize(st), "gqt_kb_moments");
     if (flag & 16) throw Error(GQT_ETIMEOUT, "gqt_kb_moments: a bounded tensor-core wait gave up");

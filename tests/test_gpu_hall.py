@@ -129,6 +129,9 @@ def test_hall_argument_errors():
         g.gqt_kb_moments(g.gqt_build_hamiltonian(blk, dE), torch.from_numpy(S.random_phase(blk.n, 1)).cuda(), 1, 8,
                          0, 1, lam)
     assert e.value.status == g.GQT_EINVAL
+    with pytest.raises(g.GqtError) as e:
+        g.gqt_set_kb_contraction(g.gqt_build_hamiltonian(lat, dE), 2)
+    assert e.value.status == g.GQT_EINVAL
     sig = torch.empty(3, dtype=torch.float64, device="cuda")
     for bad in ([0.1, 0.0, 0.2], [-dE, 0.0, 0.1]):
         with pytest.raises(g.GqtError) as e:
@@ -145,12 +148,13 @@ def _gpu_lambda_tc(lat, dE, ph, M, a, b):
 
 
 @pytest.mark.parametrize("name", ["haldane", "square_phases", "honeycomb_real"])
-@pytest.mark.parametrize("M,R", [(1, 1), (17, 2), (70, 1), (130, 3)])
+@pytest.mark.parametrize("M,R", [(1, 1), (17, 2), (70, 1), (130, 3), (300, 1)])
 @pytest.mark.parametrize("pair", ["xy", "yx", "xx"])
 def test_kb_moments_tensor_core_contraction(name, M, R, pair):
     """Split-TF32 contraction on the tcgen05 tensor cores (three products per pair,
     FP32 accumulation per split, FP64 sum of splits): within 1e-5 of the oracle
-    (normalised by the largest moment), including partial 128 x 128 tiles."""
+    (normalised by the largest moment), including partial 128 x 256 tiles and
+    contraction lengths N R that are not a multiple of the 8-site chunk."""
     lat, dE = _model(name)
     ph = S.random_phase(lat.n, R, seed=33)
     d = {"x": (0, lat.dx), "y": (1, lat.dy)}
@@ -170,7 +174,8 @@ def test_haldane_chern_plateau_tensor_core():
     M = 256
     E = torch.from_numpy(np.linspace(-0.97 * dE, 0.0, 3001)).cuda()
     out = {}
-    for name, lam in (("tc", _gpu_lambda_tc(lat, dE, basis, M, 0, 1)), ("fp64", _gpu_lambda(lat, dE, basis, M, 0, 1))):
+    for name, lam in (("tc", _gpu_lambda_tc(lat, dE, basis, M, 0, 1)),
+                      ("fp64", _gpu_lambda(lat, dE, basis, M, 0, 1))):
         sig = torch.empty(E.numel(), dtype=torch.float64, device="cuda")
         g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
         out[name] = sig.cpu().numpy()
@@ -181,9 +186,9 @@ def test_haldane_chern_plateau_tensor_core():
 
 def test_kb_moments_tensor_core_full_size_lattice():
     """Tensor-core contraction on the 512 x 512 Haldane lattice (N = 524,288) at
-    M = 64.  Each split accumulates about 16K products in FP32, whose rounding
-    grows like sqrt(16384) * 2^-24 = 8e-6 of the split's magnitude; the bound is
-    5e-5 of the largest moment (measured: 1.3e-5)."""
+    M = 64.  Each split accumulates at most 8192 sites' products in FP32, whose
+    rounding grows like sqrt(8192) * 2^-24 = 5e-6 of the split's magnitude; the
+    bound is 5e-5 of the largest moment (measured: 1.3e-5)."""
     lat = S.haldane(512, 512, -1.0, 0.15, math.pi / 2, 0.0, 1.0, seed=1705013875)
     dE = 1.05 * (3 + 6 * 0.15 + 0.5)
     ph = S.random_phase(lat.n, 1, seed=1705013875)
@@ -257,7 +262,8 @@ def test_haldane_chern_plateau_fp32_chains():
     M = 256
     E = torch.from_numpy(np.linspace(-0.97 * dE, 0.0, 3001)).cuda()
     out = {}
-    for name, lam in (("fp32", _gpu_lambda_fp32(lat, dE, basis, M, 0, 1)), ("fp64", _gpu_lambda(lat, dE, basis, M, 0, 1))):
+    for name, lam in (("fp32", _gpu_lambda_fp32(lat, dE, basis, M, 0, 1)),
+                      ("fp64", _gpu_lambda(lat, dE, basis, M, 0, 1))):
         sig = torch.empty(E.numel(), dtype=torch.float64, device="cuda")
         g.gqt_kubo_bastin(lam, E, dE, lat.volume, sig)
         out[name] = sig.cpu().numpy()
