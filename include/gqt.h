@@ -228,8 +228,11 @@ gqt_status gqt_kb_moments(gqt_ham* ham, const void* d_r, int R, int M, int alpha
  * 0 = FP64 (complex FP64 GEMM on the FP64 pipe; Lambda to FP64 rounding);
  * 1 = split TF32 on the tcgen05 tensor cores: both stacks are rounded to pairs of
  *     TF32 numbers (hi + lo, about 22 bits), each product is hi*hi + hi*lo + lo*hi,
- *     accumulated in FP32 over splits of about 16K terms and summed in FP64
- *     (Lambda to about 1e-6 of its largest entries).  The chains stay FP64. */
+ *     accumulated in FP32 over splits of at most 8192 sites and summed in FP64
+ *     (Lambda to about 1e-5 of its largest entries).  The chains run in the
+ *     handle's precision (FP64, or FP32 for GQT_FP32_ACC64 handles, which
+ *     require this mode).
+ * Other values: GQT_EINVAL. */
 gqt_status gqt_set_kb_contraction(gqt_ham* ham, int mode);
 
 /* sigma_ab(E_j) in units of e^2/h at zero temperature from Kubo-Bastin moments:
