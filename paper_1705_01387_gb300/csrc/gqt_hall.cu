@@ -184,14 +184,49 @@ __global__ void __launch_bounds__(256) k_kb_step(HallEll<F64, CH> H,
     const int r = (int)(e - i * R);
     const S dg = H.diag2[i];
     V a = mk(V(), (S)0, (S)0), q = a, b = a;
-    for (int k = 0; k < H.K; ++k) {
-      const size_t sl = (size_t)k * H.n + i;
-      const size_t j = (size_t)H.idx[sl] * R + r;
-      const auto h2 = H.hop2[sl];
-      const V qj = qk[j];
-      q = mla(q, h2, qj);
-      b = mla(b, vh[sl], qj);
-      if (!last) a = mla(a, h2, pk[j]);
+    if constexpr (F64) {
+      // bound by the FP64 pipe: one slot at a time
+      for (int k = 0; k < H.K; ++k) {
+        const size_t sl = (size_t)k * H.n + i;
+        const size_t j = (size_t)H.idx[sl] * R + r;
+        const auto h2 = H.hop2[sl];
+        const V qj = qk[j];
+        q = mla(q, h2, qj);
+        b = mla(b, vh[sl], qj);
+        if (!last) a = mla(a, h2, pk[j]);
+      }
+    } else {
+      // FP32 storage: slots in groups of KG -- the group's indices and hoppings,
+      // then its gathers, then the multiply-adds in slot order (the order of the
+      // one-slot loop), so that more gathers are in flight
+      constexpr int KG = 4;
+      using HT = typename HallEll<F64, CH>::HT;
+      for (int k0 = 0; k0 < H.K; k0 += KG) {
+        size_t jj[KG];
+        HT hh[KG], vv[KG];
+        V qq[KG], pp[KG];
+#pragma unroll
+        for (int u = 0; u < KG; ++u)
+          if (k0 + u < H.K) {
+            const size_t sl = (size_t)(k0 + u) * H.n + i;
+            jj[u] = (size_t)H.idx[sl] * R + r;
+            hh[u] = H.hop2[sl];
+            vv[u] = vh[sl];
+          }
+#pragma unroll
+        for (int u = 0; u < KG; ++u)
+          if (k0 + u < H.K) {
+            qq[u] = qk[jj[u]];
+            if (!last) pp[u] = pk[jj[u]];
+          }
+#pragma unroll
+        for (int u = 0; u < KG; ++u)
+          if (k0 + u < H.K) {
+            q = mla(q, hh[u], qq[u]);
+            b = mla(b, vv[u], qq[u]);
+            if (!last) a = mla(a, hh[u], pp[u]);
+          }
+      }
     }
     const V bv = mk(V(), (S)-0.5 * b.y, (S)0.5 * b.x);
     if (bout) bout[e] = bv;
@@ -656,6 +691,8 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
   const size_t total = (size_t)h->n * R;
   const size_t vb = total * sizeof(V);
   const int g = grid_for(total);
+  // FP32 chain steps: one element per thread (every neighbour gather in flight at once)
+  const int gs = F64 ? g : (int)std::min<size_t>((total + 255) / 256, (size_t)INT32_MAX);
   V* Q = (V*)h->ws(WS_HALL_Q, vb * 3).p;
   auto qbuf = [&](int k) -> V* { return Q + (size_t)(k % 3) * total; };
   const size_t mm = (size_t)M * M;
@@ -734,7 +771,7 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
     const V* qk = k == 0 ? r : qbuf(k);
     const V* qkm1 = k == 0 ? nullptr : (k == 1 ? r : qbuf(k - 1));
     const size_t pe = prof_begin(st);
-    k_kb_step<F64, CH><<<g, 256, 0, st>>>(H, vh, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
+    k_kb_step<F64, CH><<<gs, 256, 0, st>>>(H, vh, R, total, pbuf(k), k == 0 ? nullptr : pbuf(k - 1),
                                       last ? nullptr : pbuf(k + 1), qk, qkm1, last ? nullptr : qbuf(k + 1), nullptr,
                                       k == 0, last, last ? none : planes(0, k + 1), planes(4, k));
     check_launch("k_kb_step");
