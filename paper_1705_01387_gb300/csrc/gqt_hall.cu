@@ -16,8 +16,10 @@
 // stacks P (M vectors) and B (M vectors).  k_kb_gemm forms all M x M inner
 // products <P_m|B_n> -- a dense complex contraction over N*R, the dominant cost
 // (4 M^2 N R FP64 FMAs) -- as a register-blocked FP64 GEMM with a deterministic
-// split over the contraction.  k_kb_integrand evaluates the double sum on an
-// energy grid (a bilinear form per energy), and k_kb_scan integrates it.
+// split over the contraction; k_kb_gemm_tma does the same contraction in split
+// TF32 on the tcgen05 tensor cores, its operands brought in by TMA.
+// k_kb_integrand evaluates the double sum on an energy grid (a bilinear form per
+// energy), and k_kb_scan integrates it.
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
