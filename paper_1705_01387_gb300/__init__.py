@@ -325,14 +325,16 @@ def gqt_kpm_weights(M: int, E, w, energy_scale: float, n_over_omega: float, beta
 
 def gqt_kb_moments(ham: Ham, r, R: int, M: int, alpha: int, beta: int, lam, stream=None):
     """Kubo-Bastin moments Lambda [M, M] (CUDA complex128) of directions alpha, beta
-    (0 = x, 1 = y) from R unit vectors r (CUDA complex128 [N, R])."""
+    (0 = x, 1 = y) from R unit vectors r (CUDA [N, R]: complex128 for an FP64
+    handle; complex64 for an FP32 handle, which needs gqt_set_kb_contraction(ham, 1))."""
     _check(lib().gqt_kb_moments(ham.ptr, _dptr(r, "r"), int(R), int(M), int(alpha), int(beta), _dptr(lam, "lam"),
                                 _stream(stream)))
     return lam
 
 
 def gqt_set_kb_contraction(ham: Ham, mode: int):
-    """0 = FP64 contraction of the Hall moments (default), 1 = split TF32 on the tensor cores."""
+    """0 = FP64 contraction of the Hall moments (default); 1 = split TF32 on the
+    tcgen05 tensor cores (Lambda to about 1e-5 of its largest entry)."""
     _check(lib().gqt_set_kb_contraction(ham.ptr, int(mode)))
 
 
