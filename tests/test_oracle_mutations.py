@@ -60,6 +60,7 @@ PINS = [
     lambda: P.test_vac_moments_match_definition("square", True),
     lambda: P.test_msd_moments_match_definition("square", True),
     lambda: P.test_jackson_kernel_properties(),
+    lambda: P.test_jackson_kernel_autocorrelation_form(),
     lambda: P.test_kpm_normalisation_chebyshev_gauss(),
     lambda: P.test_kpm_chain_band_centre(),
     lambda: P.test_sigma_rules(),
@@ -97,5 +98,24 @@ def test_pins_catch_planted_mistake(workdir, name, old, new):
             except AssertionError:
                 caught.append(pin)
         assert caught, f"no pin caught the planted mistake: {name}"
+    finally:
+        O.use_library(None)
+
+
+def test_jackson_mutation_caught_by_autocorrelation_pin_alone(workdir):
+    """The Jackson kernel's alpha (Eq. 31) is pinned by its autocorrelation construction,
+    not only by properties that a wrong alpha also satisfies."""
+    src = open(SRC).read()
+    old, new = "const double a = 1.0 / (M + 1.0);", "const double a = 1.0 / M;"
+    path = os.path.join(workdir, "mut_jackson_alone.cpp")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = path[:-4] + ".so"
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-o", so, path])
+    O.use_library(so)
+    try:
+        P.test_jackson_kernel_properties()  # the properties alone do not see it
+        with pytest.raises(AssertionError):
+            P.test_jackson_kernel_autocorrelation_form()
     finally:
         O.use_library(None)
