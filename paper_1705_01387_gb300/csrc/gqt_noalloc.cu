@@ -10,6 +10,7 @@
 // placed in one file-scope device array of fixed size.  The paper has no
 // counterpart to this; it is a deployment convenience.
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,9 +24,14 @@
 
 // The kernel templates are compiled into this translation unit under their own
 // namespace so that its instantiations never collide with the main library's.
+// Their system headers are included above, at file scope; the macro keeps
+// gqt_kernels.cuh from including any header inside the namespace, so a header it
+// needs and this file lacks is a compile error rather than a silent rebinding.
+#define GQT_KERNELS_NO_SYSTEM_INCLUDES 1
 namespace gqt_na {
 #include "gqt_kernels.cuh"
 }
+#undef GQT_KERNELS_NO_SYSTEM_INCLUDES
 
 using gqt::Error;
 using gqt_na::gqt::Ell;
@@ -43,20 +49,55 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
+CUcontext g_noalloc_ctx[kMaxDevices] = {};
 
-// Set-up, once per device, with that device current.
+// The current context of the calling thread (the driver's cuCtxGetCurrent,
+// looked up once through the runtime, so the library links no driver stub).
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext*);
+  static const Fn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q);
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (Fn)p : nullptr;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) throw gqt::Error(GQT_ECUDA, "cuCtxGetCurrent is not available from the driver");
+  return c;
+}
+
+// Set-up, once per device, with that device current: the array's device
+// address.  The address belongs to the device's context; if that context was
+// destroyed and created again (cudaDeviceReset), the module is loaded anew and
+// the address is looked up again.
 void* scratch_address(int dev) {
   using namespace gqt;
   if (dev < 0 || dev >= kMaxDevices) throw Error(GQT_EINVAL, "device ordinal out of range for the scratch table");
+  // The caller's earlier runtime calls (pointer checks) made the device's
+  // primary context current on this thread.
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
       throw Error(GQT_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     g_noalloc_addr[dev] = p;
+    g_noalloc_ctx[dev] = ctx;
   }
   return g_noalloc_addr[dev];
+}
+
+// EINVAL unless p is device memory of device dev.
+void require_device_pointer(const void* p, int dev, const char* what) {
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();
+    throw gqt::Error(GQT_EINVAL, std::string("gqt_dos_moments_noalloc: ") + what + " is not a CUDA pointer");
+  }
+  if (pa.type != cudaMemoryTypeDevice || pa.device != dev)
+    throw gqt::Error(GQT_EINVAL, std::string("gqt_dos_moments_noalloc: ") + what +
+                                     " must be device memory of the handle's device");
 }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -116,6 +157,7 @@ void run(const gqt_ham* h, const void* phi, int R, int rs, int M, double* d_mu, 
 
 extern "C" gqt_status gqt_dos_moments_noalloc(const gqt_ham* h, const void* d_phi, int R, int M, double* d_mu,
                                               void* stream) {
+  gqt::NvtxRange nvtx_call_(__func__);
   using namespace gqt;
   try {
     if (!h || !d_phi || !d_mu || M < 1) throw Error(GQT_EINVAL, "gqt_dos_moments_noalloc: bad argument");
@@ -125,11 +167,8 @@ extern "C" gqt_status gqt_dos_moments_noalloc(const gqt_ham* h, const void* d_ph
     int dev = -1;
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != h->device) throw Error(GQT_EINVAL, "the current CUDA device is not the handle's device");
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, d_mu) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
-      cudaGetLastError();
-      throw Error(GQT_EINVAL, "gqt_dos_moments_noalloc writes device memory only: d_mu must be a device pointer");
-    }
+    require_device_pointer(d_phi, dev, "d_phi");
+    require_device_pointer(d_mu, dev, "d_mu");
     cudaStream_t st = (cudaStream_t)stream;
     int rs = 0;
     while ((1 << rs) < R) ++rs;
