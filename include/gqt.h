@@ -235,6 +235,20 @@ gqt_status gqt_kb_moments(gqt_ham* ham, const void* d_r, int R, int M, int alpha
  * Other values: GQT_EINVAL. */
 gqt_status gqt_set_kb_contraction(gqt_ham* ham, int mode);
 
+/* Polls of each bounded device wait of the handle's kernels (default 2^24, a
+ * few tenths of a second to seconds; 0 = give up at once).  The only kernel
+ * that waits is the tensor-core Hall contraction (gqt_set_kb_contraction mode
+ * 1): its single issuing thread waits on mbarriers for the bulk tensor copies of
+ * each stage and for the commit of the products that read a buffer.  A wait that
+ * runs out stops the pipeline; the thread then drains what is in flight (the
+ * last committed products and the issued copies, 2^24 polls each, independent of
+ * this setting), frees its tensor memory and the call returns GQT_ETIMEOUT; the
+ * moments it wrote are not valid.  The handle stays usable.  This is the library's failure
+ * detection for a device wait that never completes (Sec. 4.2 names a too-small
+ * energy scale as the method's failure mode; a stalled copy engine is the
+ * hardware's).  polls < 0: GQT_EINVAL. */
+gqt_status gqt_set_wait_limit(gqt_ham* ham, int polls);
+
 /* sigma_ab(E_j) in units of e^2/h at zero temperature from Kubo-Bastin moments:
  *   sigma(E_j) = (2/area) int_{x_0}^{x_j} dx F(x),  x = E/dE = cos th,
  *   F(x) = (1 - x^2)^-2 Re sum_mn c_m c_n g_m g_n Gamma_mn(x) Lambda_mn,
@@ -367,9 +381,12 @@ gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);
  *  - Limit: 2*n*R*e + (max(M,2)+1)*nb*R*16 + a few KB must fit in the array
  *    (e = 16 bytes FP64 / 8 bytes FP32 per element, nb = min(2*SMs,
  *    ceil(n*R/1024)) CTAs); larger requests return GQT_EINVAL naming the size.
- *  - Single-segment handles only.  d_phi: device [n][R]; d_mu: DEVICE memory,
- *    nseg*R*M doubles (Re <phi|T_m|phi>); the handle must have been built earlier.
- *  - The first call on a device looks up the array's device address on that
+ *  - Single-segment handles only.  d_phi: device [n][R] of the handle's device;
+ *    d_mu: DEVICE memory of the same device, nseg*R*M doubles
+ *    (Re <phi|T_m|phi>); the handle must have been built earlier.  A host
+ *    pointer or another device's pointer returns GQT_EINVAL.
+ *  - The first call on a device (and the first after that device's context was
+ *    destroyed and created again) looks up the array's device address on that
  *    device (cudaGetSymbolAddress); make that first call before any stream
  *    capture.
  *  - Every call shares the one array and it keeps the previous call's contents

@@ -58,6 +58,7 @@ _SIGS = {
     "gqt_kpm_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _P],
     "gqt_kb_moments": [_P, _P, _I, _I, _I, _I, _P, _P],
     "gqt_set_kb_contraction": [_P, _I],
+    "gqt_set_wait_limit": [_P, _I],
     "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kubo_bastin_fermi": [_P, _I, _P, _I, _D, _D, _I, _P, _I, _D, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
@@ -336,6 +337,12 @@ def gqt_set_kb_contraction(ham: Ham, mode: int):
     """0 = FP64 contraction of the Hall moments (default); 1 = split TF32 on the
     tcgen05 tensor cores (Lambda to about 1e-5 of its largest entry)."""
     _check(lib().gqt_set_kb_contraction(ham.ptr, int(mode)))
+
+
+def gqt_set_wait_limit(ham: Ham, polls: int):
+    """Polls of each bounded device wait of the handle's kernels (default 2**24;
+    0 gives up at once); a wait that runs out makes the call return GQT_ETIMEOUT."""
+    _check(lib().gqt_set_wait_limit(ham.ptr, int(polls)))
 
 
 def gqt_kubo_bastin(lam, E, energy_scale: float, area: float, sigma, kernel: int = 0, stream=None):

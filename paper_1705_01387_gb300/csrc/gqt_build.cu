@@ -266,6 +266,7 @@ gqt_ham::~gqt_ham() {
 
 extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double energy_scale, gqt_precision precision,
                                             const int64_t* seg_offsets, int nseg, gqt_ham** out) {
+  gqt::NvtxRange nvtx_call_(__func__);
   try {
     if (!lattice || !out) throw Error(GQT_EINVAL, "null argument");
     *out = nullptr;
@@ -448,6 +449,7 @@ extern "C" gqt_status gqt_generate_lattice(const gqt_lattice* lattice, int64_t* 
 // into the same device arrays, so cached graphs and workspace stay valid.
 extern "C" gqt_status gqt_update_hamiltonian(gqt_ham* h, const double* onsite, const double* hop_re,
                                              const double* hop_im) {
+  gqt::NvtxRange nvtx_call_(__func__);
   try {
     if (!h || !hop_re) throw Error(GQT_EINVAL, "gqt_update_hamiltonian: null argument");
     if (h->h_idx.empty()) throw Error(GQT_EINVAL, "gqt_update_hamiltonian: handle has no host topology");

@@ -317,14 +317,18 @@ __global__ void __launch_bounds__(256, 2) k_kb_gemm(const double2* __restrict__ 
 // with
 //   Re Lambda = Pre.Bre + Pim.Bim,  Im Lambda = Pre.Bim - Pim.Bre
 // every operand is a plain tile of a plane.
+// Polls of the drain after a timeout (copies and products still in flight);
+// the pipeline's own waits take the handle's limit (gqt_set_wait_limit, by
+// default the same number).
 constexpr int TC_WAIT_LIMIT = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier; false on timeout.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the completion of phase `parity` of an mbarrier: at most
+// `limit` polls (0: give up at once); false on timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int limit) {
   uint32_t done = 0;
-  for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+  for (int it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -355,8 +359,12 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // past M read as zeros) that complete on the stage's mbarrier, the products of
 // a stage go out as soon as it has landed,
 // and a buffer is refilled, NBUF - 1 stages ahead, once the products that read
-// it have completed.  Every wait is bounded; after a timeout the thread drains
-// what is still in flight (again bounded) and the kernel reports it.
+// it have completed.  Every wait is bounded (wait_limit polls); after a timeout
+// the thread drains what is still in flight (the last committed products and
+// the copies issued but not waited for, TC_WAIT_LIMIT polls each) and the
+// kernel reports it (err bit 16; bit 32 if the drain gave up as well).  The
+// tensor memory is freed in every case: a CTA that exited holding it would make
+// the next CTA's allocation on that SM wait without end.
 constexpr int TM_TM = 128, TM_TN = 256, TM_TK = 8;       // 8 FP32 sites: one 32-B swizzle span per row
 constexpr int TM_ATILE = TM_TM * 32, TM_BTILE = TM_TN * 32;  // 4 KB, 8 KB
 constexpr int TM_BOX = 128 * 32;                            // one copy: 8 sites x 128 rows
@@ -398,7 +406,7 @@ struct TmPlanes {
 
 __global__ void __launch_bounds__(TM_THREADS, 1) k_kb_gemm_tma(const __grid_constant__ CUtensorMap map, TmPlanes pz,
                                                         int M, size_t kt, size_t kchunk, double2* __restrict__ part,
-                                                        int* __restrict__ err) {
+                                                        int* __restrict__ err, int wait_limit) {
   extern __shared__ __align__(1024) unsigned char tm_raw[];
   const uint32_t raw = smem_addr(tm_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzled tiles start on 1 KB
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_kb_gemm_tma(const __grid_cons
     for (; issued < nst && issued < TM_NBUF; ++issued) issue(issued);
     for (int s = 0; s < nst; ++s) {
       const int b = s % TM_NBUF;
-      if (!tc_wait(&full[b], (uint32_t)((s / TM_NBUF) & 1))) {
+      if (!tc_wait(&full[b], (uint32_t)((s / TM_NBUF) & 1), wait_limit)) {
         ok = false;
         break;
       }
@@ -483,22 +491,24 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_kb_gemm_tma(const __grid_cons
       // s - 1 + NBUF while those of stage s run
       if (s >= 1 && issued < nst) {
         const int p = s - 1;
-        if (!tc_wait(&done[p % TM_NBUF], (uint32_t)((p / TM_NBUF) & 1))) {
+        if (!tc_wait(&done[p % TM_NBUF], (uint32_t)((p / TM_NBUF) & 1), wait_limit)) {
           ok = false;
           break;
         }
         issue(issued++);
       }
     }
-    // the last products (their completion implies that of all earlier ones); after
-    // a timeout also the copies still in flight
-    if (committed > 0 && !tc_wait(&done[(committed - 1) % TM_NBUF], (uint32_t)(((committed - 1) / TM_NBUF) & 1)))
-      ok = false;
-    if (!ok)
-      for (int s = landed; s < issued; ++s) tc_wait(&full[s % TM_NBUF], (uint32_t)((s / TM_NBUF) & 1));
+    // the last products (their completion implies that of all earlier ones)
+    const int lb = (committed - 1) % TM_NBUF;
+    const uint32_t lp = (uint32_t)(((committed - 1) / TM_NBUF) & 1);
+    if (ok && committed > 0 && !tc_wait(&done[lb], lp, wait_limit)) ok = false;
     if (!ok) {
+      // drain: the last committed products, then the copies still in flight
+      bool drained = committed == 0 || tc_wait(&done[lb], lp, TC_WAIT_LIMIT);
+      for (int s = landed; s < issued; ++s) drained = tc_wait(&full[s % TM_NBUF], (uint32_t)((s / TM_NBUF) & 1),
+                                                               TC_WAIT_LIMIT) && drained;
       *okp = 0;
-      atomicOr(err, 16);
+      atomicOr(err, drained ? 16 : (16 | 32));
     }
   }
   __syncthreads();
@@ -818,7 +828,7 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
              "smem attribute");
   const size_t pg = prof_begin(st);
   k_kb_gemm_tma<<<dim3(tm, tn, (unsigned)S), TM_THREADS, TM_SMEM, st>>>(map, pz, M, kt, kchunk, part,
-                                                                        (int*)h->d_flag.p);
+                                                                        (int*)h->d_flag.p, h->wait_limit);
   check_launch("k_kb_gemm_tma");
   prof_end(pg, 8, st);
   k_kb_reduce<<<(int)std::min<size_t>((mm + 255) / 256, 4096), 256, 0, st>>>(part, (int)S, M, (double)h->n / R,
@@ -830,6 +840,7 @@ void kb_moments_impl(gqt_ham* h, const void* rv, int R, int M, const DA* da, con
 
 extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, int alpha, int beta,
                                      double* d_lambda, void* stream) {
+  gqt::NvtxRange nvtx_call_(__func__);
   try {
     if (!h || !d_r || !d_lambda || R < 1 || M < 1 || alpha < 0 || alpha > 1 || beta < 0 || beta > 1)
       throw Error(GQT_EINVAL, "gqt_kb_moments: bad argument");
@@ -868,6 +879,9 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
     if (h->kb_mode != 0)
       check_cuda(cudaMemcpyAsync(&flag, h->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     check_cuda(cudaStreamSynchronize(st), "gqt_kb_moments");
+    if (flag & 32)
+      throw Error(GQT_ETIMEOUT, "gqt_kb_moments: a bounded tensor-core wait gave up and so did the drain of the "
+                                "copies and products in flight: later results in this CUDA context are not trusted");
     if (flag & 16) throw Error(GQT_ETIMEOUT, "gqt_kb_moments: a bounded tensor-core wait gave up");
     return GQT_OK;
   } catch (const Error& e) {
@@ -880,6 +894,15 @@ extern "C" gqt_status gqt_kb_moments(gqt_ham* h, const void* d_r, int R, int M, 
     set_error(std::string("internal error: ") + e.what());
     return GQT_ECUDA;
   }
+}
+
+extern "C" gqt_status gqt_set_wait_limit(gqt_ham* h, int polls) {
+  if (!h || polls < 0) {
+    set_error("gqt_set_wait_limit: bad argument");
+    return GQT_EINVAL;
+  }
+  h->wait_limit = polls;
+  return GQT_OK;
 }
 
 extern "C" gqt_status gqt_set_kb_contraction(gqt_ham* h, int mode) {
@@ -944,6 +967,7 @@ static std::vector<double> check_energies(const double* d_E, int NE, double ener
 
 extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const double* d_E, int NE, double energy_scale,
                                       double area, int kernel, double* d_sigma, void* stream) {
+  gqt::NvtxRange nvtx_call_(__func__);
   try {
     if (!d_lambda || !d_E || !d_sigma || M < 1 || M > 8192 || NE < 1 || !(energy_scale > 0) || !(area > 0) ||
         kernel < 0 || kernel > 1)
@@ -978,6 +1002,7 @@ extern "C" gqt_status gqt_kubo_bastin(const double* d_lambda, int M, const doubl
 extern "C" gqt_status gqt_kubo_bastin_fermi(const double* d_lambda, int M, const double* d_E, int NE,
                                             double energy_scale, double area, int kernel, const double* d_mu, int Nmu,
                                             double kT, double* d_sigma, void* stream) {
+  gqt::NvtxRange nvtx_call_(__func__);
   try {
     if (!d_lambda || !d_E || !d_mu || !d_sigma || M < 1 || M > 8192 || NE < 2 || Nmu < 1 || !(energy_scale > 0) ||
         !(area > 0) || kernel < 0 || kernel > 1 || !(kT >= 0) || !std::isfinite(kT))

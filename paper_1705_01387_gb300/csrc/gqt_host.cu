@@ -963,7 +963,9 @@ void gqt::launch_velocity(gqt_ham* h, const void* x, void* y, void* ycopy, int R
 
 // ====================================================================== API helpers
 
-#define API_BEGIN try {
+#define API_BEGIN \
+  gqt::NvtxRange nvtx_call_(__func__); \
+  try {
 #define API_END                                        \
   }                                                    \
   catch (const Error& e) {                             \
@@ -1279,6 +1281,7 @@ gqt_status gqt_vac_moments(gqt_ham* h, void* d_a, void* d_b, int R, const double
   double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
   void* l = h->ws(WS_L, h->vec_bytes(R)).p;
   for (int k = 0; k < Nt; ++k) {
+    NvtxRange step("gqt_vac_moments time step");
     const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
     const auto c = evolve_coefs(h->dE * dt[k], -1, np);
     launch_velocity(h, d_a, l, nullptr, R, st);
@@ -1302,6 +1305,7 @@ gqt_status gqt_msd_moments(gqt_ham* h, void* d_p, void* d_px, int R, const doubl
   const bool host = is_host_ptr(mu);
   double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
   for (int k = 0; k < Nt; ++k) {
+    NvtxRange step("gqt_msd_moments time step");
     const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
     const auto c = evolve_coefs(h->dE * dt[k], +1, np);
     launch_msd_step(h, d_p, d_px, R, c, st);

@@ -10,9 +10,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gqt.h"
 
 namespace gqt {
+
+// NVTX range for the lifetime of the object: every C-ABI call and every time
+// step of the VAC and MSD loops is one named range on the host timeline (seen
+// by Nsight Systems and usable as an ncu --nvtx-include filter).  Header-only
+// NVTX 3: without a tool attached a push/pop is a null-injection check.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Error : std::runtime_error {
   gqt_status code;
@@ -95,6 +108,7 @@ struct gqt_ham {
   bool use_cluster = true;  // cluster-resident moment rows for small systems
   bool use_pair = true;     // l != r moment rows by two recurrences (two moments per step)
   int kb_mode = 0;          // Hall moment contraction: 0 FP64, 1 split TF32 on the tensor cores
+  int wait_limit = 1 << 24; // polls of each bounded device wait (gqt_set_wait_limit)
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

@@ -17,9 +17,15 @@
 // Vectors: [n][R], element (i, r) at i*R + r, complex V = double2 or float2.
 #pragma once
 
+// A translation unit that includes this file inside a namespace of its own
+// includes these headers first, at file scope, and defines
+// GQT_KERNELS_NO_SYSTEM_INCLUDES, so that no system declaration lands in its
+// namespace.
+#ifndef GQT_KERNELS_NO_SYSTEM_INCLUDES
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
+#endif
 
 namespace gqt {
 

@@ -184,6 +184,35 @@ def test_haldane_chern_plateau_tensor_core():
     assert diff < 1e-4, diff
 
 
+def test_tensor_core_wait_timeout_then_recovers():
+    """Failure detection of the bounded device waits: with a wait limit of 0 polls every
+    mbarrier wait of the tensor-core contraction's pipeline gives up at once (a wait
+    that runs out, with no copy withheld and nothing faulted); the issuing thread then
+    drains the copies it issued with the fixed drain limit, frees tensor memory, and
+    the call returns GQT_ETIMEOUT.  With the default limit restored, the next call on
+    the same handle matches the oracle to the contraction's 1e-5 bound."""
+    lat = S.haldane(23, 19, -1.0, 0.15, math.pi / 2, 0.0, 1.0, seed=7)
+    dE = 1.05 * (3 + 6 * 0.15 + 0.5)
+    ph = S.random_phase(lat.n, 1, seed=35)
+    M = 256
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    g.gqt_set_kb_contraction(ham, 1)
+    r = torch.from_numpy(ph).cuda()
+    lam = torch.empty((M, M), dtype=torch.complex128, device="cuda")
+    g.gqt_set_wait_limit(ham, 0)
+    with pytest.raises(g.GqtError) as ei:
+        g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+    assert ei.value.status == g.GQT_ETIMEOUT
+    assert "drain" not in str(ei.value)  # the drain collected every copy in flight
+    with pytest.raises(g.GqtError):
+        g.gqt_set_wait_limit(ham, -1)
+    g.gqt_set_wait_limit(ham, 1 << 24)
+    g.gqt_kb_moments(ham, r, 1, M, 0, 1, lam)
+    ref = O.Hamiltonian(lat, dE).kb_moments(lat.dx, lat.dy, ph, M)
+    err = nerr(lam.cpu().numpy(), ref)
+    assert err < 1e-5, err
+
+
 def test_kb_moments_tensor_core_full_size_lattice():
     """Tensor-core contraction on the 512 x 512 Haldane lattice (N = 524,288) at
     M = 64.  Each split accumulates at most 8192 sites' products in FP32, whose
