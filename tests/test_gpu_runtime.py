@@ -86,8 +86,8 @@ def test_time_loop_is_resumable():
     assert nerr(np.concatenate([m1, m2]), m_all) < 1e-13
 
 
-def _ball(lat, centre, radius):
-    """Sites within `radius` hops of `centre` and the induced model (same H entries)."""
+def _ball_sites(lat, centre, radius):
+    """Sites within `radius` hops of `centre`."""
     dist = {centre: 0}
     frontier = [centre]
     for d in range(radius):
@@ -99,7 +99,12 @@ def _ball(lat, centre, radius):
                     dist[j] = d + 1
                     nxt.append(j)
         frontier = nxt
-    sites = np.array(sorted(dist))
+    return list(dist)
+
+
+def _ball(lat, centre, radius):
+    """Sites within `radius` hops of `centre` and the induced model (same H entries)."""
+    sites = np.array(sorted(_ball_sites(lat, centre, radius)))
     pos = {s: q for q, s in enumerate(sites)}
     n, K = sites.size, lat.max_nb
     sub = S.Lattice("ball", n, K, np.zeros(n, np.int32), np.zeros((n, K), np.int32), np.zeros((n, K), np.complex128),
@@ -118,15 +123,73 @@ def _ball(lat, centre, radius):
     return sub, pos[centre]
 
 
+@pytest.fixture(scope="module")
+def c2():
+    """The benchmark's workload: honeycomb 4096 x 2048 (N = 16,777,216), W = 2 eV, FP64."""
+    w = S.config(1)
+    lat = S.build_lattice(w.lattice_args, w.seed)
+    ham = g.gqt_build_hamiltonian(lat, w.energy_scale)
+    return w, lat, ham
+
+
+def _local_start(lat, centre, seed):
+    """Unit vector with random phases and magnitudes on the sites within 2 hops of
+    `centre` (not an eigenvector of anything, not symmetric under V)."""
+    sites = np.array(sorted(_ball_sites(lat, centre, 2)))
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(0.5, 1.0, sites.size) * np.exp(2j * np.pi * rng.uniform(size=sites.size))
+    return sites, v / np.linalg.norm(v)
+
+
 @pytest.mark.slow
-def test_full_size_sampled_local_moments():
+@pytest.mark.parametrize("kind", ["vac", "msd"])
+def test_full_size_vac_and_msd_rows_at_benchmark_launch_shape(c2, kind):
+    """The VAC row kernel (two recurrences, k_cheb_pair_w) and the MSD row (k_msd_evolve,
+    k_cheb_dbl_w) on the full benchmark lattice, launched exactly as the benchmark
+    launches them (R = 1, N = 16.8M, every CTA of the wavefront grid), against the
+    oracle on a ball of the same lattice.  The start vector lives within 2 hops of a
+    sampled site i; two steps of a short dt (N_p = 12) make the second VAC row an
+    l != r product (l = V U a, r = U V a).  A row moment after k steps is a closed walk
+    from the start support of length <= 2k(N_p - 1) + 2 + n, so the truncated ball of
+    radius Nt N_p + M/2 + 4 around i gives exactly the full lattice's values (Eqs. 17,
+    18, 22, 29, 30).  Tolerance 1e-10 normalised per row."""
+    w, lat, ham = c2
+    dE = w.energy_scale
+    M, dts = 40, np.array([0.05, 0.05])
+    Np = [g.gqt_np_rule(dE * d, 4096) for d in dts]
+    assert Np[0] == O.np_rule(dE * dts[0], 4096)
+    rng = np.random.default_rng(17 if kind == "vac" else 19)
+    for i in rng.choice(lat.n, 2, replace=False):
+        sites, v = _local_start(lat, int(i), int(i))
+        phi = torch.zeros((lat.n, 1), dtype=torch.complex128, device="cuda")
+        phi[torch.from_numpy(sites).cuda(), 0] = torch.from_numpy(v).cuda()
+        x, y = torch.empty_like(phi), torch.empty_like(phi)
+        got = np.empty((len(dts), 1, 1, M))
+        if kind == "vac":
+            g.gqt_vac_init(ham, phi, x, y, 1)
+            g.gqt_vac_moments(ham, x, y, 1, dts, M, got, Np=Np)
+        else:
+            g.gqt_msd_init(ham, phi, x, y, 1)
+            g.gqt_msd_moments(ham, x, y, 1, dts, M, got, Np=Np)
+        radius = len(dts) * max(Np) + M // 2 + 4
+        sub, _ = _ball(lat, int(i), radius)
+        pos = {s: q for q, s in enumerate(sorted(_ball_sites(lat, int(i), radius)))}
+        ps = np.zeros(sub.n, np.complex128)
+        for s_, val in zip(sites, v):
+            ps[pos[int(s_)]] = val
+        h = O.Hamiltonian(sub, dE)
+        ref = h.vac_moments(ps, dts, Np, M) if kind == "vac" else h.msd_moments(ps, dts, Np, M)
+        for k in range(len(dts)):
+            assert nerr(got[k, 0, 0], ref[k]) < 1e-10, (kind, int(i), k)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_local_moments(c2):
     """Honeycomb 4096 x 2048 (N = 16,777,216), FP64, the benchmark's launch shape:
     local moments <e_i|T_m(H~)|e_i> for sampled sites i, m < 40, equal the oracle's on
     the ball of radius 20 around i (closed walks of length m stay within m/2 hops)."""
-    w = S.config(1)
-    lat = S.build_lattice(w.lattice_args, w.seed)
+    w, lat, ham = c2
     dE = w.energy_scale
-    ham = g.gqt_build_hamiltonian(lat, dE)
     M = 40
     rng = np.random.default_rng(5)
     for i in rng.choice(lat.n, 3, replace=False):

@@ -137,6 +137,46 @@ def test_np_rule_values():
     assert O.np_rule(8.7675 * 2 / 2.7, 64) == 28
 
 
+@pytest.mark.parametrize("x", [41.0, 410.0])
+def test_long_expansions_bessel_and_np_rule(x):
+    """The long steps of the paper's localized example (Sec. 5, dt up to 100 with
+    dE = 4.1, i.e. x = dE dt up to 410 and N_p = 487 Bessel orders, Eq. 17): the
+    oracle's J_m(x) against scipy for every order used, the sum rule
+    J_0 + 2 sum J_2k = 1, and N_p = 1 + max{m: |J_m(x)| >= 1e-15} without the cap."""
+    m = np.arange(1200)
+    ref_np = 1 + int(np.max(m[np.abs(sp.jv(m, x)) >= 1e-15]))
+    assert O.np_rule(x, 4096) == ref_np
+    J = O.bessel(x, ref_np)
+    assert np.max(np.abs(J - sp.jv(np.arange(ref_np), x))) < 5e-14
+    assert abs(J[0] + 2 * J[2::2].sum() - 1.0) < 5e-14
+    if x == 410.0:
+        assert ref_np == 487  # the paper's longest step, dt = 100 at dE = 4.1
+
+
+@pytest.mark.parametrize("x", [41.0, 410.0])
+def test_long_evolution_matches_matrix_exponential(x):
+    """Eq. 17 and Eqs. 18, 22, 24 with hundreds of Bessel orders (the localized
+    example's steps) on a disordered chain, against exp(-i x H~) and the
+    Daleckii-Krein [X, U] from the eigendecomposition."""
+    lat = S.chain(61, -1.0, 4.0, seed=21)
+    dE = 4.1
+    h = O.Hamiltonian(lat, dE)
+    psi = S.random_phase(lat.n, 1, seed=22)[:, 0]
+    dt = x / dE
+    Np = O.np_rule(x, 4096)
+    lam, Q = D.eig(D.dense_h(lat, dE))
+    for sign in (+1, -1):
+        U = D.fun_of_h(lam, Q, lambda l: np.exp(-1j * sign * l * x))
+        got = h.evolve(psi, dt, sign, Np)
+        assert np.max(np.abs(got - U @ psi)) < 1e-12
+        assert abs(np.linalg.norm(got) - 1.0) < 1e-12
+    XU = D.frechet(lam, Q, lambda l: np.exp(-1j * l * x), lambda l: -1j * x * np.exp(-1j * l * x),
+                   D.dense_xh(lat, dE))
+    ref = XU @ psi
+    got = h.commutator_evolve(psi, dt, Np)
+    assert np.max(np.abs(got - ref)) < 1e-11 * max(1.0, float(np.max(np.abs(ref))))
+
+
 @pytest.mark.parametrize("kind,phases", MODELS)
 @pytest.mark.parametrize("sign", [+1, -1])
 def test_evolution_matches_matrix_exponential(kind, phases, sign):
