@@ -112,11 +112,16 @@ def test_example2_localized_chain_reduced():
     assert nerr(rd.cpu().numpy(), rd_ref) < TOL64
     assert nerr(rm.cpu().numpy(), rm_ref) < TOL64
     assert nerr(sm.cpu().numpy(), sm_ref) < 1e-9
+    # L = 2 sqrt(rho dX^2 / rho) divides by the DOS, and each energy sums 500
+    # moments: normalised noise of 1e-10 on the oracle's moments (the moment
+    # tolerance) moves L by up to 2.7e-6 of its largest value where the DOS is above
+    # 1% of its maximum (the band tails are left out), so the bound is 1e-5.
     Lg = A.propagation_length(rd.cpu().numpy()[0], rm.cpu().numpy())
     Lo = A.propagation_length(rd_ref[0], rm_ref)
-    m = np.isfinite(Lo) & (Lo > 0)
-    assert np.array_equal(m, np.isfinite(Lg) & (Lg > 0))
-    assert nerr(Lg[m], Lo[m]) < 1e-9
+    inner = rd_ref[0] > 1e-2 * rd_ref[0].max()
+    m = np.isfinite(Lo) & (Lo > 0) & inner[None, :]
+    assert np.array_equal(m, np.isfinite(Lg) & (Lg > 0) & inner[None, :])
+    assert nerr(Lg[m], Lo[m]) < 1e-5
 
 
 def test_example1_diffusive_square_reduced():
@@ -171,12 +176,15 @@ def test_example1_diffusive_square_reduced():
         assert nerr(got.cpu().numpy(), ref) < TOL64
     assert nerr(sv.cpu().numpy(), sv_ref) < 1e-9
     assert nerr(sm.cpu().numpy(), sm_ref) < 1e-9
+    inner = (np.abs(E) < 3.5) & (rd_ref[0] > 1e-3 * rd_ref[0].max())
     sc_g = A.semiclassical(rd.cpu().numpy()[0], rv.cpu().numpy(), sv.cpu().numpy())
     sc_o = A.semiclassical(rd_ref[0], rv_ref, sv_ref)
-    # energies inside the band where the DOS and velocity are well away from zero
-    inner = (np.abs(E) < 3.5) & (rd_ref[0] > 1e-3 * rd_ref[0].max())
+    # energies inside the band where the DOS and velocity are well away from zero;
+    # these quantities divide by the DOS and velocity, and normalised noise of 1e-10
+    # on the oracle's moments (the moment tolerance) moves them by up to 4.5e-9
+    # (sigma_sc, v, tau, mean free path) and 3.4e-8 (L) of their largest values
     for key in ("sigma_sc", "velocity", "tau", "mfp"):
         assert nerr(sc_g[key][inner], sc_o[key][inner]) < 1e-8, key
     Lg = A.propagation_length(rd.cpu().numpy()[0], rm.cpu().numpy())
     Lo = A.propagation_length(rd_ref[0], rm_ref)
-    assert nerr(Lg[:, inner], Lo[:, inner]) < 1e-9
+    assert nerr(Lg[:, inner], Lo[:, inner]) < 1e-7

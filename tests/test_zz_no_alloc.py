@@ -25,9 +25,13 @@ pytestmark = pytest.mark.gpu
 
 # Normalised L-infinity tolerances (max_n |d mu_n| / max_n |mu_n|): FP64 storage
 # 1e-10 against the oracle; FP32 storage 1e-5 against the oracle (the FP32 moment
-# bound of the parity tests); the same kernel through both entry points agrees to
-# 1e-12 (the two differ only in where their scratch lives and in the CTA split).
+# bound of the parity tests).  The two entry points run different recursions (the
+# regular one the l = r doubling identities, or a cluster-resident row on small
+# systems; this one the plain three-term recursion of Eq. 21), so they agree to
+# FP64 rounding (1e-12) on FP64 handles and to FP32 storage rounding (1e-5, the
+# same bound as against the oracle) on FP32 handles.
 TOL = {g.GQT_FP64: 1e-10, g.GQT_FP32_ACC64: 1e-5}
+TOL_SAME = {g.GQT_FP64: 1e-12, g.GQT_FP32_ACC64: 1e-5}
 
 
 def _call(ham, phi, R, M, mu):
@@ -65,7 +69,7 @@ def test_noalloc_matches_regular_entry_point_and_oracle_twice(prec, hop, R):
         assert _call(ham, phi, R, M, out) == g.GQT_OK, g.gqt_last_error()
         torch.cuda.synchronize()
         a, b = out.cpu().numpy()[0], ref.cpu().numpy()[0]
-        assert _nerr(a, b) < 1e-12
+        assert _nerr(a, b) < TOL_SAME[prec]
         # the oracle takes the vector the kernel saw (rounded to FP32 for FP32 storage)
         phi_seen = phi.cpu().to(torch.complex128).numpy()
         for r in range(R):
