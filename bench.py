@@ -156,6 +156,17 @@ def fp64_fma_per_orbital(K: int, hop_real: bool, dot: str) -> int:
     return {"re": rec + 2, "dbl": rec + 4, "pair": 2 * rec + 4}[dot]
 
 
+def df_fp32_ops_per_orbital(K: int, hop_real: bool, kind: str) -> int:
+    """FP32-pipe instructions per orbital per launch of the paired-FP32 kernels: one
+    pair multiply-accumulate (TwoProduct by FMA, three FMAs for the low parts, TwoSum
+    and two adds) is 12; a recurrence takes 2 of them per real diagonal or
+    neighbour term on each of Re, Im (4 for complex hoppings) and two 6-instruction
+    renormalisations; each Re dot takes 2 (24 instructions).  The l = r kernel runs
+    one recurrence and two dots, the two-recurrence kernel two and two."""
+    rec = 12 * (2 + K * (2 if hop_real else 4)) + 12
+    return {"dbl": rec + 48, "pair": 2 * rec + 48, "re": rec + 24}[kind]
+
+
 def fp32_batched(args, g, torch):
     """Batched FP32 form vs plain FP64 on the simple-cubic Anderson model L = 256
     (N = 16,777,216, 6 neighbours, t = -1, W = 16.5): DOS moments for R = 32 FP32
@@ -439,6 +450,7 @@ def run_ours(args):
     w, lat = workload(args.small, args.cells, args.moments)
     dE = w.energy_scale
     ham = g.gqt_build_hamiltonian(lat, dE, g.GQT_FP64)
+    g.gqt_set_fp64_arith(ham, args.fp64_arith)
     N, M, R = lat.n, w.M, 1
     Np = g.gqt_np_rule(dE * w.dt, 64)
     del lat
@@ -486,51 +498,43 @@ def run_ours(args):
     units = float(N) * 2 * M * args.steps * ws
     value = units / (t_ms * 1e-3)
 
-    # end to end through the C ABI with host buffers: the step's state vectors come
-    # from pinned host memory, the rows and the updated state go back to the host.
-    # The MSD state uploads on a copy stream while the VAC row runs, and the VAC
-    # state downloads there while the MSD row runs.
+    # end to end through the C ABI with host buffers: every step hands the library
+    # the four state vectors in pinned host memory; gqt_vac_moments and
+    # gqt_msd_moments copy them to the device and back inside the call, and the
+    # reconstructed rows (the step's result) come back to the host.
     hs = [torch.empty((N, R), dtype=cd, pin_memory=True) for _ in range(4 if not args.no_e2e else 0)]
     for h_, d_ in zip(hs, (a, b, p, px)):
         h_.copy_(d_)
-    hrows = np.empty((2, M))
-    cstream = torch.cuda.Stream()
-    main = torch.cuda.current_stream()
+    hrec = torch.empty((2, E.numel()), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps if not args.no_e2e else 0):
-        a.copy_(hs[0], non_blocking=True)
-        b.copy_(hs[1], non_blocking=True)
-        cstream.wait_stream(main)
-        with torch.cuda.stream(cstream):
-            p.copy_(hs[2], non_blocking=True)
-            px.copy_(hs[3], non_blocking=True)
-        g.gqt_vac_moments(ham, a, b, R, dts, M, hrows[0], Np=[Np])
-        main.wait_stream(cstream)
-        cstream.wait_stream(main)
-        with torch.cuda.stream(cstream):
-            hs[0].copy_(a, non_blocking=True)
-            hs[1].copy_(b, non_blocking=True)
-        g.gqt_msd_moments(ham, p, px, R, dts, M, hrows[1], Np=[Np])
-        hs[2].copy_(p, non_blocking=True)
-        hs[3].copy_(px, non_blocking=True)
+        g.gqt_vac_moments(ham, hs[0], hs[1], R, dts, M, rows[0], Np=[Np])
+        g.gqt_msd_moments(ham, hs[2], hs[3], R, dts, M, rows[1], Np=[Np])
+        g.gqt_kpm_reconstruct(rows, E, dE, nO, recon)
+        hrec.copy_(recon)
         torch.cuda.synchronize()
     t_e2e = max(time.perf_counter() - t0, 1e-9)
     vb = N * R * 16
     e2e = None if args.no_e2e else {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * vb,
-                                    "d2h_bytes_per_step": 4 * vb + 2 * M * 8}
+                                    "d2h_bytes_per_step": 4 * vb + hrec.numel() * 8,
+                                    "path": "gqt_vac_moments + gqt_msd_moments on host state vectors (copied in "
+                                            "and out inside the calls) + gqt_kpm_reconstruct, result read back"}
 
     # roofline of the dominant kernel family (largest share of the timed kernel time):
     # family 1 = VAC orders Re <l|T_m|r> by one recurrence (k_cheb_re), 5 = MSD orders
     # with l = r, two moments per step (k_cheb_dbl, no l read), 6 = VAC orders by two
-    # recurrences, two moments per step (k_cheb_pair).
+    # recurrences, two moments per step (k_cheb_pair).  With paired-FP32 arithmetic
+    # (mode 1) families 5 and 6 run k_cheb_dbl_df and k_cheb_pair_df.
     hbm, peak_kind = _peaks()
+    df = args.fp64_arith == 1
+    sfx = "_df" if df else ""
     fam = {1: ("k_cheb_re (VAC row: fused SpMV + three-term recurrence + Re <l|T_m|r>)",
                bytes_per_orbital_cheb(3, True, ham.hop_real, R), "re"),
-           5: ("k_cheb_dbl (MSD row: fused SpMV + recurrence + <u_n|u_n>, <u_n+1|u_n>)",
+           5: (f"k_cheb_dbl{sfx} (MSD row: fused SpMV + recurrence + <u_n|u_n>, <u_n+1|u_n>)",
                bytes_per_orbital_cheb(3, True, ham.hop_real, R) - 16 * R, "dbl"),
-           6: ("k_cheb_pair (VAC row: two fused SpMV + recurrences, T_k l and T_k r, + Re <A_k|B_k>, Re <A_k|B_k+1>)",
-               bytes_per_orbital_pair(3, ham.hop_real, R), "pair")}
+           6: (f"k_cheb_pair{sfx} (VAC row: two fused SpMV + recurrences, T_k l and T_k r, + Re <A_k|B_k>, "
+               "Re <A_k|B_k+1>)", bytes_per_orbital_pair(3, ham.hop_real, R), "pair")}
     total_prof = float(np.sum(prof_ms))
     dom = max(fam, key=lambda k: prof_ms[k])
     fams = {}
@@ -545,38 +549,60 @@ def run_ours(args):
     n_launch = int(prof_n[dom])
     avg_s = prof_ms[dom] * 1e-3 / max(n_launch, 1)
     achieved = N * bpo / avg_s / 1e9
-    # FP64 arithmetic roofline of the same kernel against the measured FMA peak
-    fp64_peak = g.gqt_probe_fp64()
-    fma = fp64_fma_per_orbital(3, ham.hop_real, fkind) * R
-    fp64_achieved = 2.0 * fma * N / avg_s / 1e9
-    hbm_frac, alu_frac = achieved / hbm, fp64_achieved / fp64_peak
+    hbm_frac = achieved / hbm
+    clocks = clk.summary()
+    hbm_obj = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+               "traffic": traffic, "traffic_source": "profiles/traffic_moment_kernels.json (ncu at N = 4.2M, "
+                                                     "scaled by N)",
+               "kernel": kname, "bytes_per_orbital": bpo, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    if df:
+        # arithmetic roofline of the paired-FP32 kernel: FP32-pipe instructions per
+        # orbital against SMs x 128 lanes x the SM clock sampled during the timed region
+        ops = df_fp32_ops_per_orbital(3, ham.hop_real, fkind) * R
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = float(clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+        fp32_peak = sms * 128 * mhz * 1e6 / 1e9
+        fp32_achieved = ops * N / avg_s / 1e9
+        alu = {"achieved": fp32_achieved, "peak": fp32_peak, "unit": "G FP32-pipe instr/s",
+               "frac": fp32_achieved / fp32_peak, "fp32_instr_per_orbital": ops,
+               "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}
+        roof = dict(hbm_obj, fp32_pipe=alu) if hbm_frac >= alu["frac"] else \
+            {"bound": "alu", **{k: alu[k] for k in ("achieved", "peak", "unit", "frac")}, "traffic": traffic,
+             "kernel": kname, "hbm": {k: hbm_obj[k] for k in ("achieved", "peak", "unit", "frac")}}
+    else:
+        # FP64 arithmetic roofline of the same kernel against the measured FMA peak
+        fp64_peak = g.gqt_probe_fp64()
+        fma = fp64_fma_per_orbital(3, ham.hop_real, fkind) * R
+        fp64_achieved = 2.0 * fma * N / avg_s / 1e9
+        alu_frac = fp64_achieved / fp64_peak
+        roof = ({"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                 "frac": alu_frac, "traffic": traffic, "kernel": kname, "fp64_fma_per_orbital": fma,
+                 "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)",
+                 "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+                         "bytes_per_orbital": bpo}}
+                if alu_frac > hbm_frac else
+                dict(hbm_obj, fp64={"achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                                    "frac": alu_frac, "fp64_fma_per_orbital": fma}))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded Anderson honeycomb lattice and random-phase vectors)",
+        "dtype": "f32x2" if df else "f64",
+        "data": "synthetic (seeded Anderson honeycomb lattice and random-phase vectors)",
         "config": {"workload": w.name if not args.small else w.name + "_small", "n_orbitals": N, "moments": M,
                    "vectors_per_gpu": R, "bessel_orders": Np, "dt_hbar_per_eV": w.dt, "energies": int(E.numel()),
                    "step": "one VAC + MSD time step (2M moments, 2 evolutions) + KPM reconstruction",
                    "hop_storage": "real FP64" if ham.hop_real else "complex FP64",
+                   "arith": ("moment rows on pairs of FP32 numbers (double-float, ~48-bit significands; FP64 "
+                             "storage, results within 1e-12 of the FP64 mode), evolution in FP64")
+                   if df else "FP64 fused multiply-adds",
                    "l2": "inputs larger than L2 (H~ ELL %.2f GB + state vectors)" % (N * (3 * 12 + 8 + 24) / 1e9),
                    "parallelism": f"replicas x{ws} (independent random vectors)"},
         "gpu_launches": int(launches),
-        "roofline": ({"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                      "frac": alu_frac, "traffic": traffic, "kernel": kname, "fp64_fma_per_orbital": fma,
-                      "peak_source": "measured FP64 FMA probe (gqt_probe_fp64)",
-                      "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
-                              "bytes_per_orbital": bpo}}
-                     if alu_frac > hbm_frac else
-                     {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
-                      "traffic": traffic, "traffic_source": "profiles/traffic_moment_kernels.json (ncu at N = 4.2M, scaled by N)",
-                      "kernel": kname, "bytes_per_orbital": bpo,
-                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                      "fp64": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "GFLOP/s", "frac": alu_frac,
-                               "fp64_fma_per_orbital": fma}}),
+        "roofline": roof,
         "kernels": {"dominant": kname, "avg_launch_us": avg_s * 1e6, "launches": n_launch,
                     "share_of_timed_kernels": prof_ms[dom] / max(total_prof, 1e-12), "families": fams},
         "e2e": e2e,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_fp32:
         out["fp32_batched"] = fp32_batched(args, g, torch)
@@ -759,6 +785,8 @@ def main():
     ap.add_argument("--hall-L", type=int, default=0, help="Haldane cells per side of the Hall run (profiling)")
     ap.add_argument("--hall-moments", type=int, default=0, help="Kubo-Bastin moments of the Hall run (profiling)")
     ap.add_argument("--hall-skip-fp64", action="store_true", help="time only the tensor-core contraction (profiling)")
+    ap.add_argument("--fp64-arith", type=int, default=1, choices=[0, 1],
+                    help="moment rows of the FP64 workload: 1 = pairs of FP32 numbers (default), 0 = FP64 FMAs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -159,7 +159,10 @@ gqt_status gqt_vac_init(gqt_ham* ham, const void* d_phi, void* d_a, void* d_b, i
  * for k < Nt: row k = Re <V a| T_n(H~) |b>, then a, b <- U(-dt[k]) (a, b).  So rows
  * are at t, t+dt_0, ..., and on return the state is at t + sum dt (resumable).
  * dt: host [Nt]; Np: host [Nt] or NULL (rule of gqt_evolve).
- * mu: [Nt][nseg][R][M] doubles, host or device. */
+ * mu: [Nt][nseg][R][M] doubles, host or device.
+ * d_a, d_b: both device or both host memory (pinned or pageable) [n][R]; host
+ * state is copied to the device before the rows and back after them, inside the
+ * call (two n R vectors of handle workspace). */
 gqt_status gqt_vac_moments(gqt_ham* ham, void* d_a, void* d_b, int R, const double* dt, const int* Np, int Nt,
                            int M, double* mu, void* stream);
 
@@ -168,7 +171,8 @@ gqt_status gqt_msd_init(gqt_ham* ham, const void* d_phi, void* d_p, void* d_px, 
 
 /* MSD moments (Eq. 30).  On entry (d_p, d_px) = (U(t) phi, [X, U(t)] phi); for k < Nt:
  * px <- [X, U(dt_k)] p + U(dt_k) px, p <- U(dt_k) p (Eqs. 17-18), then row k =
- * Re <px| T_n(H~) |px>.  Rows are at t + dt_0, ..., t + sum dt.  Layout as VAC. */
+ * Re <px| T_n(H~) |px>.  Rows are at t + dt_0, ..., t + sum dt.  Layout and host
+ * state as VAC. */
 gqt_status gqt_msd_moments(gqt_ham* ham, void* d_p, void* d_px, int R, const double* dt, const int* Np, int Nt,
                            int M, double* mu, void* stream);
 
@@ -343,6 +347,22 @@ gqt_status gqt_set_cluster(gqt_ham* ham, int enable);
  * the multi-vector form (not the chunk-ordered variant 0 or cluster rows).  0
  * runs one recurrence on r with a dot against l per order. */
 gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
+
+/* Arithmetic of the moment rows of FP64 handles (GQT_FP64) with R = 1 (default 1):
+ * 0 = FP64 fused multiply-adds;
+ * 1 = pairs of FP32 numbers (hi + lo, about 48 significant bits; Dekker's and
+ *     Knuth's error-free sums and products on the FP32 pipes): the two-recurrence
+ *     VAC rows (gqt_vac_moments) and the l = r rows
+ *     (gqt_dos_moments, gqt_msd_moments) of lattices with 2, 3, 4 or 6 neighbour
+ *     slots.  Storage stays FP64-sized (16 bytes per complex element, the
+ *     handle's vectors complex128); moments agree with the FP64 mode to about
+ *     1e-12 of mu_0 at M = 3000.  GB300 issues 64 FP32 fused multiply-adds for
+ *     each FP64 one, so mode 1 is bound by HBM instead of the FP64 pipe.  The
+ *     first call in mode 1 splits 2H~ into pairs (K n (8 or 16) + 8 n bytes of
+ *     device memory held by the handle).
+ * Other values: GQT_EINVAL.  Evolution, velocity, adjoint and Hall kernels, and
+ * R > 1 rows, always use the FP64 pipe. */
+gqt_status gqt_set_fp64_arith(gqt_ham* ham, int mode);
 
 /* Blocked sweep order of the multi-vector kernels (default 1; built-in simple-
  * cubic lattices whose side is a power of two >= 64): the CTAs walk the x-rows in

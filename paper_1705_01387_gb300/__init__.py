@@ -59,6 +59,7 @@ _SIGS = {
     "gqt_kb_moments": [_P, _P, _I, _I, _I, _I, _P, _P],
     "gqt_set_kb_contraction": [_P, _I],
     "gqt_set_wait_limit": [_P, _I],
+    "gqt_set_fp64_arith": [_P, _I],
     "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kubo_bastin_fermi": [_P, _I, _P, _I, _D, _D, _I, _P, _I, _D, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
@@ -125,6 +126,19 @@ def _dptr(t, name="tensor"):
     if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def _state_ptr(t, name="state"):
+    """VAC/MSD state vector: a contiguous CUDA tensor, or a contiguous CPU tensor or
+    numpy array (pinned or pageable; the library copies it in and out)."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray) and t.flags.c_contiguous:
+        return C.c_void_p(t.ctypes.data)
+    raise ValueError(f"{name} must be a contiguous tensor or numpy array")
 
 
 def _out_ptr(out):
@@ -294,7 +308,7 @@ def _steps(dt, Np):
 
 def gqt_vac_moments(ham: Ham, a, b, R: int, dt, M: int, mu, Np=None, stream=None):
     dt, npp = _steps(dt, Np)
-    _check(lib().gqt_vac_moments(ham.ptr, _dptr(a, "a"), _dptr(b, "b"), int(R), dt.ctypes.data,
+    _check(lib().gqt_vac_moments(ham.ptr, _state_ptr(a, "a"), _state_ptr(b, "b"), int(R), dt.ctypes.data,
                                  None if npp is None else npp.ctypes.data, dt.size, int(M), _out_ptr(mu),
                                  _stream(stream)))
     return mu
@@ -302,7 +316,7 @@ def gqt_vac_moments(ham: Ham, a, b, R: int, dt, M: int, mu, Np=None, stream=None
 
 def gqt_msd_moments(ham: Ham, p, px, R: int, dt, M: int, mu, Np=None, stream=None):
     dt, npp = _steps(dt, Np)
-    _check(lib().gqt_msd_moments(ham.ptr, _dptr(p, "p"), _dptr(px, "px"), int(R), dt.ctypes.data,
+    _check(lib().gqt_msd_moments(ham.ptr, _state_ptr(p, "p"), _state_ptr(px, "px"), int(R), dt.ctypes.data,
                                  None if npp is None else npp.ctypes.data, dt.size, int(M), _out_ptr(mu),
                                  _stream(stream)))
     return mu
@@ -337,6 +351,12 @@ def gqt_set_kb_contraction(ham: Ham, mode: int):
     """0 = FP64 contraction of the Hall moments (default); 1 = split TF32 on the
     tcgen05 tensor cores (Lambda to about 1e-5 of its largest entry)."""
     _check(lib().gqt_set_kb_contraction(ham.ptr, int(mode)))
+
+
+def gqt_set_fp64_arith(ham: Ham, mode: int):
+    """Moment rows of an FP64 handle with one vector: 1 = pairs of FP32 numbers on the
+    FP32 pipes (default), 0 = FP64 fused multiply-adds."""
+    _check(lib().gqt_set_fp64_arith(ham.ptr, int(mode)))
 
 
 def gqt_set_wait_limit(ham: Ham, polls: int):

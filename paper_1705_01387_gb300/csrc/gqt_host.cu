@@ -25,6 +25,7 @@
 #include "gqt_internal.h"
 #include "gqt_kernels.cuh"
 #include "gqt_cluster.cuh"
+#include "gqt_df.cuh"
 
 using namespace gqt;
 
@@ -682,6 +683,151 @@ static void launch_wave_pair(gqt_ham* h, const Ell<FP64, CH>& H, const BlockTabl
 #undef GQT_PAIR
 }
 
+// ------------------------------------------------ FP64 rows on the FP32 pipes
+
+// Moment rows of FP64 handles with R = 1 run on pairs of FP32 numbers when the
+// handle's FP64 arithmetic mode is 1 (gqt_set_fp64_arith): the two-recurrence
+// VAC rows and the l = r rows, for the neighbour counts of the wavefront kernels.
+static bool df_applies(const gqt_ham* h, int R, int kind) {
+  if (!(h->prec == GQT_FP64 && h->fp64_arith == 1 && R == 1 && h->variant != 0 && h->threads <= 256)) return false;
+  if (!(h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6)) return false;
+  return kind == 2 || (kind == 1 && pair_applies(h, R));
+}
+
+// 2H~ and 2U/dE as (hi, lo) pairs, split once from the FP64 arrays (again after
+// gqt_update_hamiltonian).  Runs on the call's stream before any graph capture.
+static void ensure_df(gqt_ham* h, cudaStream_t st) {
+  if (h->df_ready) return;
+  const size_t nslots = (size_t)h->K * h->n;
+  h->d_hop_df.ensure(nslots * (h->hop_real ? sizeof(float2) : sizeof(float4)));
+  h->d_diag_df.ensure((size_t)h->n * sizeof(float2));
+  const int blocks = sm_count() * 8;
+  if (h->hop_real)
+    k_split_hamiltonian<false><<<blocks, 256, 0, st>>>((long long)nslots, h->d_hop.p, (int)h->n,
+                                                       (const double*)h->d_diag.p, h->d_hop_df.p,
+                                                       (float2*)h->d_diag_df.p);
+  else
+    k_split_hamiltonian<true><<<blocks, 256, 0, st>>>((long long)nslots, h->d_hop.p, (int)h->n,
+                                                      (const double*)h->d_diag.p, h->d_hop_df.p,
+                                                      (float2*)h->d_diag_df.p);
+  check_launch("k_split_hamiltonian");
+  h->df_ready = true;
+}
+
+template <bool CH>
+static DfEll<CH> df_ell_of(const gqt_ham* h) {
+  DfEll<CH> e;
+  e.n = (int)h->n;
+  e.K = h->K;
+  e.idx = (const int*)h->d_idx.p;
+  e.hop = (const typename DfHop<CH>::T*)h->d_hop_df.p;
+  e.diag = (const float2*)h->d_diag_df.p;
+  return e;
+}
+
+// elements in flight per thread in the l = r rows (two, within 85 registers, up
+// to four neighbour slots)
+constexpr int df_u(int KK) { return KK <= 4 ? 2 : 1; }
+
+template <bool CH, int KK>
+static int df_occupancy_k(bool pair, int threads) {
+  const void* f = pair ? (const void*)k_cheb_pair_df<CH, KK, false> : (const void*)k_cheb_dbl_df<CH, KK, df_u(KK), false>;
+  int n = 0;
+  const size_t smem = (size_t)3 * (threads / 32) * sizeof(double2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 3;
+  }
+  return std::max(1, std::min(n, 16));
+}
+
+template <bool CH>
+static int df_occupancy(int K, bool pair, int threads) {
+  switch (K) {
+    case 2: return df_occupancy_k<CH, 2>(pair, threads);
+    case 3: return df_occupancy_k<CH, 3>(pair, threads);
+    case 4: return df_occupancy_k<CH, 4>(pair, threads);
+    default: return df_occupancy_k<CH, 6>(pair, threads);
+  }
+}
+
+template <bool CH, int KK>
+static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const void* l, const void* r,
+                    float4* A1, float4* A2, float4* W1, float4* W2, double2* partial, cudaStream_t s2) {
+  const DfEll<CH> H = df_ell_of<CH>(h);
+  const int4* tab = (const int4*)T.d_tab4.p;
+  const int nb = T.nblocks;
+  const size_t sm = smem_bytes(h, 1, 3);
+  for (int m = 1; m <= std::max(steps, 1); ++m) {
+    float4* aout = (m % 2 == 1) ? A1 : A2;
+    float4* bout = (m % 2 == 1) ? W1 : W2;
+    size_t pe = prof_begin(s2);
+    if (pair) {
+      if (m == 1)
+        k_cheb_pair_df<CH, KK, true><<<nb, h->threads, sm, s2>>>(H, tab, l, r, nullptr, nullptr, aout, bout, A2, W2,
+                                                                 partial, nb, m, 2 * steps);
+      else
+        k_cheb_pair_df<CH, KK, false><<<nb, h->threads, sm, s2>>>(H, tab, (m - 1) % 2 == 1 ? A1 : A2,
+                                                                  (m - 1) % 2 == 1 ? W1 : W2, aout, bout, aout, bout,
+                                                                  nullptr, nullptr, partial, nb, m, 2 * steps);
+      check_launch("k_cheb_pair_df");
+      prof_end(pe, m == 1 ? 0 : 6, s2);
+    } else {
+      if (m == 1)
+        k_cheb_dbl_df<CH, KK, df_u(KK), true><<<nb, h->threads, sm, s2>>>(H, tab, r, nullptr, bout, W2, partial, nb, m);
+      else
+        k_cheb_dbl_df<CH, KK, df_u(KK), false><<<nb, h->threads, sm, s2>>>(H, tab, (m - 1) % 2 == 1 ? W1 : W2, bout, bout,
+                                                                       nullptr, partial, nb, m);
+      check_launch("k_cheb_dbl_df");
+      prof_end(pe, m == 1 ? 0 : 5, s2);
+    }
+  }
+}
+
+// kind 1 (two-recurrence VAC rows) or 2 (l = r rows) of an FP64 handle, R = 1,
+// on the FP32 pipes; same partial slots and reduction as the FP64 kernels.
+static void launch_moments_df(gqt_ham* h, const void* l, const void* r, int M, void* out, int kind,
+                              cudaStream_t st) {
+  ensure_df(h, st);
+  const bool pair = kind == 1;
+  const int occ = h->blocks_per_sm > 0 ? h->blocks_per_sm
+                                       : (h->hop_real ? df_occupancy<false>(h->K, pair, h->threads)
+                                                      : df_occupancy<true>(h->K, pair, h->threads));
+  const BlockTable& T = h->table(1, occ);
+  const int nb = T.nblocks;
+  const size_t vb = h->vec_bytes(1);
+  float4* W1 = (float4*)h->ws(WS_T1, vb).p;
+  float4* W2 = (float4*)h->ws(WS_T2, vb).p;
+  float4* A1 = pair ? (float4*)h->ws(WS_PA1, vb).p : nullptr;
+  float4* A2 = pair ? (float4*)h->ws(WS_PA2, vb).p : nullptr;
+  const int slots = std::max(M, 2) + 2;
+  double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * std::max(nb, 16) * sizeof(double2)).p;
+  const int steps = (M + 1) / 2;
+  const double tol = 1e-6;
+  const size_t total = (size_t)h->nseg * M;
+  const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
+  const std::string key = key_of("momdf", {l, r, out, W1, W2, A1, A2, partial, T.d_blk.p},
+                                 {(double)kind, (double)M, (double)h->threads, (double)nb});
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    auto rows = [&](auto ch) {
+      constexpr bool CH = decltype(ch)::value;
+      switch (h->K) {
+        case 2: df_rows<CH, 2>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
+        case 3: df_rows<CH, 3>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
+        case 4: df_rows<CH, 4>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
+        default: df_rows<CH, 6>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
+      }
+    };
+    if (h->hop_real)
+      rows(std::integral_constant<bool, false>());
+    else
+      rows(std::integral_constant<bool, true>());
+    k_reduce_dbl<<<rb, 256, 0, s2>>>(partial, M, nb, 1, (const int*)T.d_seg_blk.p, h->nseg, 1.0 + tol, (double*)out,
+                                     (int*)h->d_flag.p, pair ? 2 * steps : -1);
+    check_launch("k_reduce_dbl");
+  });
+}
+
 // Launch the moment recursion of r against l and reduce into out, layout
 // [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
 // (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
@@ -727,6 +873,10 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       check_launch("k_reduce(cluster)");
       return;
     }
+  }
+  if (df_applies(h, R, kind)) {
+    launch_moments_df(h, l, r, M, out, kind, st);
+    return;
   }
   const bool pair = kind == 1 && pair_applies(h, R);
   void* wa1 = pair ? h->ws(WS_PA1, vb).p : nullptr;
@@ -1012,6 +1162,40 @@ static void deliver(const void* dsrc, double* dst, size_t bytes, cudaStream_t st
     check_cuda(cudaMemcpyAsync(dst, dsrc, bytes, cudaMemcpyDeviceToDevice, st), "result copy");
 }
 
+// State vectors of the VAC and MSD rows may live in host memory (pinned or
+// pageable): they are copied into two workspace slots of the handle before the
+// call's kernels and back after them, on the call's stream.
+struct StagedPair {
+  void* x = nullptr;
+  void* y = nullptr;
+  void* hx = nullptr;
+  void* hy = nullptr;
+  size_t bytes = 0;
+};
+
+static StagedPair stage_in(gqt_ham* h, void* x, void* y, int R, cudaStream_t st) {
+  const bool hx = is_host_ptr(x), hy = is_host_ptr(y);
+  require(hx == hy, "the two state vectors must both be device memory or both host memory");
+  StagedPair s;
+  s.x = x;
+  s.y = y;
+  if (!hx) return s;
+  s.bytes = h->vec_bytes(R);
+  s.hx = x;
+  s.hy = y;
+  s.x = h->ws(WS_STAGE0, s.bytes).p;
+  s.y = h->ws(WS_STAGE0 + 1, s.bytes).p;
+  check_cuda(cudaMemcpyAsync(s.x, x, s.bytes, cudaMemcpyHostToDevice, st), "state upload");
+  check_cuda(cudaMemcpyAsync(s.y, y, s.bytes, cudaMemcpyHostToDevice, st), "state upload");
+  return s;
+}
+
+static void stage_out(const StagedPair& s, cudaStream_t st) {
+  if (!s.hx) return;
+  check_cuda(cudaMemcpyAsync(s.hx, s.x, s.bytes, cudaMemcpyDeviceToHost, st), "state download");
+  check_cuda(cudaMemcpyAsync(s.hy, s.y, s.bytes, cudaMemcpyDeviceToHost, st), "state download");
+}
+
 static int resolve_np(gqt_ham* h, double dt, int Np) {
   require(std::isfinite(dt) && dt >= 0.0, "time step must be finite and >= 0");
   if (Np > 0) return Np;
@@ -1100,6 +1284,13 @@ gqt_status gqt_set_vac_pair(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_pair = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_fp64_arith(gqt_ham* h, int mode) {
+  API_BEGIN
+  require(h != nullptr && (mode == 0 || mode == 1), "gqt_set_fp64_arith: mode must be 0 or 1");
+  h->fp64_arith = mode;
   API_END
 }
 
@@ -1280,15 +1471,19 @@ gqt_status gqt_vac_moments(gqt_ham* h, void* d_a, void* d_b, int R, const double
   const bool host = is_host_ptr(mu);
   double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
   void* l = h->ws(WS_L, h->vec_bytes(R)).p;
+  const StagedPair sp = stage_in(h, d_a, d_b, R, st);
+  void* a = sp.x;
+  void* b = sp.y;
   for (int k = 0; k < Nt; ++k) {
     NvtxRange step("gqt_vac_moments time step");
     const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
     const auto c = evolve_coefs(h->dE * dt[k], -1, np);
-    launch_velocity(h, d_a, l, nullptr, R, st);
-    launch_moments(h, l, d_b, R, M, dmu + k * row, 1, st);
-    void* sets[2] = {d_a, d_b};
+    launch_velocity(h, a, l, nullptr, R, st);
+    launch_moments(h, l, b, R, M, dmu + k * row, 1, st);
+    void* sets[2] = {a, b};
     launch_evolve_sets<2>(h, sets, R, c, st, nullptr);
   }
+  stage_out(sp, st);
   if (host && Nt > 0) deliver(dmu, mu, Nt * row * sizeof(double), st);
   return finish_call(h, st, "gqt_vac_moments");
   API_END
@@ -1304,13 +1499,17 @@ gqt_status gqt_msd_moments(gqt_ham* h, void* d_p, void* d_px, int R, const doubl
   const size_t row = (size_t)h->nseg * R * M;
   const bool host = is_host_ptr(mu);
   double* dmu = host ? (double*)h->ws(WS_MU, std::max<size_t>(1, Nt * row) * sizeof(double)).p : mu;
+  const StagedPair sp = stage_in(h, d_p, d_px, R, st);
+  void* p = sp.x;
+  void* px = sp.y;
   for (int k = 0; k < Nt; ++k) {
     NvtxRange step("gqt_msd_moments time step");
     const int np = resolve_np(h, dt[k], Np ? Np[k] : 0);
     const auto c = evolve_coefs(h->dE * dt[k], +1, np);
-    launch_msd_step(h, d_p, d_px, R, c, st);
-    launch_moments(h, d_px, d_px, R, M, dmu + k * row, 2, st);
+    launch_msd_step(h, p, px, R, c, st);
+    launch_moments(h, px, px, R, M, dmu + k * row, 2, st);
   }
+  stage_out(sp, st);
   if (host && Nt > 0) deliver(dmu, mu, Nt * row * sizeof(double), st);
   return finish_call(h, st, "gqt_msd_moments");
   API_END

@@ -74,7 +74,8 @@ enum WorkSlot {
   WS_CLUSTER_SEG = 17,
   WS_PA1 = 18,  // chain A buffers of the two-recurrence (pair) moment rows
   WS_PA2 = 19,
-  WS_ADJ0 = 20  // adjoint workspace slots start here
+  WS_ADJ0 = 20,  // adjoint workspace slots start here
+  WS_STAGE0 = 96  // +0, +1: host-resident VAC/MSD state staged on the device
 };
 
 uint64_t splitmix_mix(uint64_t z);
@@ -109,6 +110,9 @@ struct gqt_ham {
   bool use_pair = true;     // l != r moment rows by two recurrences (two moments per step)
   int kb_mode = 0;          // Hall moment contraction: 0 FP64, 1 split TF32 on the tensor cores
   int wait_limit = 1 << 24; // polls of each bounded device wait (gqt_set_wait_limit)
+  int fp64_arith = 1;       // FP64 handles' R = 1 moment rows: 0 FP64 pipe, 1 pairs of FP32 (gqt_set_fp64_arith)
+  gqt::DevBuf d_hop_df, d_diag_df;  // 2H~ and 2U/dE as (hi, lo) FP32 pairs, split on first use
+  bool df_ready = false;
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

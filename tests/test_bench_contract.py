@@ -38,4 +38,6 @@ def test_gpu_arm_json():
     assert r["bound"] in ("hbm", "alu") and r["peak"] > 0 and 0 < r["frac"] < 1.5
     assert d["gpu_launches"] > 0 and d["value"] > 0 and d["e2e"]["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
-    assert d["dtype"] == "f64" and d["scaling"] == "weak"
+    # the FP64 workload's moment rows run on pairs of FP32 numbers by default
+    assert d["dtype"] in ("f64", "f32x2") and d["scaling"] == "weak"
+    assert "arith" in d["config"]

@@ -1,0 +1,174 @@
+"""FP64 moment rows computed on pairs of FP32 numbers (gqt_set_fp64_arith mode 1,
+the default for FP64 handles with one vector) through the C ABI.
+
+The kernels k_cheb_pair_df (VAC rows by two recurrences) and k_cheb_dbl_df (l = r
+rows: DOS, MSD) keep FP64-sized storage and carry about 48 significant bits in
+their arithmetic (hi + lo pairs with error-free sums and products).  They must
+meet the FP64 bar: 1e-10 normalised against the serial FP64 oracle, on every
+neighbour count they serve (2, 3, 4, 6 slots), real and complex hoppings, tiny
+and odd M, several CTAs with a ragged tail, several segments, and at the full
+benchmark size against the FP64-pipe mode (gqt_set_fp64_arith mode 0).  The
+cluster-resident rows (small systems) are switched off so that the wavefront
+kernels run at these sizes.
+"""
+import numpy as np
+import pytest
+
+import gqt_synth as S
+import oracle as O
+
+torch = pytest.importorskip("torch")
+g = pytest.importorskip("paper_1705_01387_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def nerr(x, y):
+    x = np.asarray(x)
+    y = np.asarray(y)
+    return float(np.max(np.abs(x - y)) / max(float(np.max(np.abs(y))), 1e-300))
+
+
+MODELS = {
+    "honeycomb37x23": lambda: (S.honeycomb(37, 23, -2.7, 2.0, seed=3), S.energy_scale_rule(3, -2.7, 2.0)),
+    "honeycomb37x23_phases": lambda: (S.with_random_bond_phases(S.honeycomb(37, 23, -2.7, 2.0, seed=3), 4),
+                                      S.energy_scale_rule(3, -2.7, 2.0)),
+    "square41x29": lambda: (S.square(41, 29, -1.0, 4.0, seed=5), S.energy_scale_rule(4, -1.0, 4.0)),
+    "cubic13": lambda: (S.cubic(13, -1.0, 16.5, seed=7), S.energy_scale_rule(6, -1.0, 16.5)),
+    "chain5001": lambda: (S.chain(5001, -1.0, 4.0, seed=9), S.energy_scale_rule(2, -1.0, 4.0)),
+}
+
+
+def _ham(lat, dE, mode=1):
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    g.gqt_set_cluster(ham, False)
+    g.gqt_set_fp64_arith(ham, mode)
+    return ham
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+@pytest.mark.parametrize("M", [1, 2, 3, 257])
+def test_df_rows_match_oracle(name, M):
+    """DOS (l = r), VAC (l != r, two recurrences) and MSD rows of two time steps."""
+    lat, dE = MODELS[name]()
+    ham = _ham(lat, dE)
+    h = O.Hamiltonian(lat, dE)
+    phi = S.random_phase(lat.n, 1, seed=M)
+    d = torch.from_numpy(phi).cuda()
+    dos = np.empty((1, 1, M))
+    g.gqt_dos_moments(ham, d, 1, M, dos)
+    assert nerr(dos.ravel(), h.dos_moments(phi[:, 0], M).real) < TOL64
+    dts = np.array([0.4, 0.7])
+    Np = [O.np_rule(dE * t, 64) for t in dts]
+    a, b = torch.empty_like(d), torch.empty_like(d)
+    g.gqt_vac_init(ham, d, a, b, 1)
+    vac = np.empty((2, 1, 1, M))
+    g.gqt_vac_moments(ham, a, b, 1, dts, M, vac, Np=Np)
+    assert nerr(vac.reshape(2, M), h.vac_moments(phi[:, 0], dts, Np, M)) < TOL64
+    p, px = torch.empty_like(d), torch.empty_like(d)
+    g.gqt_msd_init(ham, d, p, px, 1)
+    msd = np.empty((2, 1, 1, M))
+    g.gqt_msd_moments(ham, p, px, 1, dts, M, msd, Np=Np)
+    assert nerr(msd.reshape(2, M), h.msd_moments(phi[:, 0], dts, Np, M)) < TOL64
+
+
+@pytest.mark.parametrize("name", ["honeycomb37x23", "honeycomb37x23_phases", "cubic13"])
+def test_df_and_fp64_modes_agree(name):
+    """The same rows in both arithmetic modes: within 1e-12 (measured about 2e-15)."""
+    lat, dE = MODELS[name]()
+    phi = torch.from_numpy(S.random_phase(lat.n, 1, seed=12)).cuda()
+    M = 600
+    rows = {}
+    for mode in (0, 1):
+        ham = _ham(lat, dE, mode)
+        dos = np.empty((1, 1, M))
+        g.gqt_dos_moments(ham, phi, 1, M, dos)
+        a, b = torch.empty_like(phi), torch.empty_like(phi)
+        g.gqt_vac_init(ham, phi, a, b, 1)
+        vac = np.empty((1, 1, 1, M))
+        g.gqt_vac_moments(ham, a, b, 1, [0.5], M, vac)
+        rows[mode] = (dos.ravel(), vac.ravel())
+    for k in range(2):
+        assert nerr(rows[1][k], rows[0][k]) < 1e-12
+
+
+def test_df_ragged_segments_match_separate_builds():
+    """Several segments in one handle (block-diagonal realisations): per-segment DOS
+    and VAC moments equal the oracle on each realisation."""
+    parts = [S.honeycomb(L1, L2, -2.7, 2.0, seed=40 + q) for q, (L1, L2) in enumerate(((9, 7), (13, 5), (6, 6)))]
+    blk = S.block_diagonal(parts)
+    dE = S.energy_scale_rule(3, -2.7, 2.0)
+    ham = _ham(blk, dE)
+    assert ham.nseg == 3
+    phi = torch.empty((blk.n, 1), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, 78, 1, phi)
+    M = 129
+    mu = np.empty((3, 1, M))
+    g.gqt_dos_moments(ham, phi, 1, M, mu)
+    a, b = torch.empty_like(phi), torch.empty_like(phi)
+    g.gqt_vac_init(ham, phi, a, b, 1)
+    vac = np.empty((1, 3, 1, M))
+    g.gqt_vac_moments(ham, a, b, 1, [0.3], M, vac)
+    ph = phi.cpu().numpy()[:, 0]
+    for q, p in enumerate(parts):
+        o = blk.seg_offsets[q]
+        h = O.Hamiltonian(p, dE)
+        assert nerr(mu[q, 0], h.dos_moments(ph[o:o + p.n], M).real) < TOL64
+        ref = h.vac_moments(ph[o:o + p.n], [0.3], [O.np_rule(dE * 0.3, 64)], M)
+        assert nerr(vac[0, q, 0], ref[0]) < TOL64
+
+
+def test_df_split_follows_hamiltonian_updates():
+    """gqt_update_hamiltonian invalidates the (hi, lo) split of 2H~: moments after an
+    update equal the oracle on the updated model."""
+    lat, dE = MODELS["square41x29"]()
+    ham = _ham(lat, dE)
+    phi = torch.from_numpy(S.random_phase(lat.n, 1, seed=3)).cuda()
+    M = 200
+    mu = np.empty((1, 1, M))
+    g.gqt_dos_moments(ham, phi, 1, M, mu)  # builds the split of the first model
+    rng = np.random.default_rng(4)
+    lat.onsite = rng.uniform(-1.5, 1.5, lat.n)
+    lat.hop = lat.hop * 0.9
+    g.gqt_update_hamiltonian(ham, lat.onsite, lat.hop)
+    g.gqt_dos_moments(ham, phi, 1, M, mu)
+    ref = O.Hamiltonian(lat, dE).dos_moments(phi.cpu().numpy()[:, 0], M).real
+    assert nerr(mu.ravel(), ref) < TOL64
+
+
+def test_df_mode_argument():
+    lat, dE = MODELS["chain5001"]()
+    ham = g.gqt_build_hamiltonian(lat, dE)
+    with pytest.raises(g.GqtError) as e:
+        g.gqt_set_fp64_arith(ham, 2)
+    assert e.value.status == g.GQT_EINVAL
+
+
+@pytest.mark.slow
+def test_df_full_size_agrees_with_fp64_mode():
+    """Honeycomb 4096 x 2048 (N = 16,777,216), the benchmark's rows at M = 3000: DOS,
+    one VAC row and one MSD row in both modes agree to 1e-12 of their largest moment
+    (measured 2e-15); the FP64 mode is itself oracle-checked at this size on balls of
+    the lattice (test_gpu_runtime.py)."""
+    ham = g.gqt_build_hamiltonian(None, 9.555, g.GQT_FP64, kind=g.GQT_LATTICE_HONEYCOMB, L1=4096, L2=2048, t=-2.7,
+                                  W=2.0, seed=S.BASE_SEED + 1)
+    N = 4096 * 2048 * 2
+    phi = torch.empty((N, 1), dtype=torch.complex128, device="cuda")
+    g.gqt_random_phase(ham, S.BASE_SEED + 1, 1, phi)
+    M, dt = 3000, 2.0 / 2.7
+    rows = {}
+    for mode in (0, 1):
+        g.gqt_set_fp64_arith(ham, mode)
+        a, b, p, px = (torch.empty_like(phi) for _ in range(4))
+        g.gqt_vac_init(ham, phi, a, b, 1)
+        g.gqt_msd_init(ham, phi, p, px, 1)
+        dos, vac, msd = np.empty((1, 1, M)), np.empty((1, 1, 1, M)), np.empty((1, 1, 1, M))
+        g.gqt_dos_moments(ham, phi, 1, M, dos)
+        g.gqt_vac_moments(ham, a, b, 1, [dt], M, vac)
+        g.gqt_msd_moments(ham, p, px, 1, [dt], M, msd)
+        rows[mode] = (dos.ravel(), vac.ravel(), msd.ravel())
+    for k in range(3):
+        assert nerr(rows[1][k], rows[0][k]) < 1e-12, k
+    assert abs(rows[1][0][0] - 1.0) < 1e-13
