@@ -233,62 +233,94 @@ def precision_table(args, g, torch):
     """Per-result error of the FP32-storage form against the FP64 path on the
     honeycomb 2048 x 2048 lattice with 1% vacancies (N = 8,388,608, W = 0.5 eV,
     R = 8, M = 4000, dt = 2 hbar/|t|): DOS moments and reconstructed DOS, VAC
-    moments, rho*C_vv(E) and sigma_VAC(E, t) over the first steps, MSD moments,
-    rho*dX^2(E) and sigma_MSD.  Errors are normalised L-infinity over E (and n)."""
+    moments, rho*C_vv(E, t) and sigma_VAC(E, t) over Nt steps (default 200, the
+    workload's count), MSD moments, rho*dX^2(E) and sigma_MSD over the first
+    --precision-msd-steps steps.  The FP32 form runs all R vectors in one batched
+    handle; the FP64 reference runs the first --precision-ref-vectors of the same
+    random-phase vectors one at a time (R = 1 rows of an FP64 handle).  Errors are
+    normalised L-infinity over n (moments) or E, per vector, maximised over the
+    reference vectors and rows; the VAC row error is also reported per step."""
     w = S.config(3, small=args.small)
     L1 = w.lattice_args["L1"]
     M, R, Nt = w.M, w.R, args.precision_steps
+    nref = max(1, min(args.precision_ref_vectors, R))
+    Nm = max(1, min(args.precision_msd_steps, Nt))
     dE = w.energy_scale
-    res = {}
     E = torch.from_numpy(w.energies).cuda()
     dts = np.full(Nt, w.dt)
-    for prec in (g.GQT_FP64, g.GQT_FP32_ACC64):
+
+    def run(prec, R_, first):
         ham = g.gqt_build_hamiltonian(None, dE, prec, kind=g.GQT_LATTICE_HONEYCOMB, L1=L1, L2=L1, t=-2.7, W=0.5,
                                       vacancy_frac=0.01, seed=w.seed)
         nO = ham.n / ham.volume
         cd = torch.complex128 if prec == g.GQT_FP64 else torch.complex64
-        phi = torch.empty((ham.n, R), dtype=cd, device="cuda")
-        g.gqt_random_phase(ham, w.seed, R, phi)
-        dos = torch.empty((1, R, M), dtype=torch.float64, device="cuda")
-        g.gqt_dos_moments(ham, phi, R, M, dos)
+        phi = torch.empty((ham.n, R_), dtype=cd, device="cuda")
+        g.gqt_random_phase(ham, w.seed, R_, phi, first_vector=first)
+        dos = torch.empty((1, R_, M), dtype=torch.float64, device="cuda")
+        g.gqt_dos_moments(ham, phi, R_, M, dos)
         a, b = torch.empty_like(phi), torch.empty_like(phi)
-        g.gqt_vac_init(ham, phi, a, b, R)
-        vac = torch.empty((Nt, 1, R, M), dtype=torch.float64, device="cuda")
+        g.gqt_vac_init(ham, phi, a, b, R_)
+        vac = torch.empty((Nt, 1, R_, M), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.gqt_vac_moments(ham, a, b, R, dts, M, vac)
+        g.gqt_vac_moments(ham, a, b, R_, dts, M, vac)
         torch.cuda.synchronize()
         t_vac = time.perf_counter() - t0
         p, px = torch.empty_like(phi), torch.empty_like(phi)
-        g.gqt_msd_init(ham, phi, p, px, R)
-        msd = torch.empty((Nt, 1, R, M), dtype=torch.float64, device="cuda")
-        g.gqt_msd_moments(ham, p, px, R, dts, M, msd)
+        g.gqt_msd_init(ham, phi, p, px, R_)
+        msd = torch.empty((Nm, 1, R_, M), dtype=torch.float64, device="cuda")
+        g.gqt_msd_moments(ham, p, px, R_, dts[:Nm], M, msd)
         out = {"dos_mu": dos[0].cpu().numpy(), "vac_mu": vac[:, 0].cpu().numpy(), "msd_mu": msd[:, 0].cpu().numpy(),
-               "t_vac": t_vac}
-        # reconstruction, vector 0 (rows over time)
-        for key, rows in (("dos", dos[0, :1]), ("vac", vac[:, 0, 0].contiguous()), ("msd", msd[:, 0, 0].contiguous())):
+               "t_vac": t_vac, "n": ham.n}
+        # reconstruction of every vector's rows, then sigma over time
+        for key, rows in (("dos", dos[0]), ("vac", vac[:, 0].transpose(0, 1).reshape(R_ * Nt, M)),
+                          ("msd", msd[:, 0].transpose(0, 1).reshape(R_ * Nm, M))):
             rec = torch.empty((rows.shape[0], E.numel()), dtype=torch.float64, device="cuda")
             g.gqt_kpm_reconstruct(rows.contiguous(), E, dE, nO, rec)
             out[key] = rec
-        sv = torch.empty_like(out["vac"])
-        g.gqt_sigma_vac(out["vac"], dts, sv)
-        sm = torch.empty_like(out["msd"])
-        g.gqt_sigma_msd(out["msd"], dts, sm)
-        out["sigma_vac"], out["sigma_msd"] = sv, sm
+        out["vac"] = out["vac"].view(R_, Nt, -1)
+        out["msd"] = out["msd"].view(R_, Nm, -1)
+        sv, sm = [], []
+        for r in range(R_):
+            s1 = torch.empty_like(out["vac"][r])
+            g.gqt_sigma_vac(out["vac"][r].contiguous(), dts, s1)
+            s2 = torch.empty_like(out["msd"][r])
+            g.gqt_sigma_msd(out["msd"][r].contiguous(), dts[:Nm], s2)
+            sv.append(s1)
+            sm.append(s2)
+        out["sigma_vac"], out["sigma_msd"] = torch.stack(sv), torch.stack(sm)
         for k in ("dos", "vac", "msd", "sigma_vac", "sigma_msd"):
             out[k] = out[k].cpu().numpy()
-        res[prec] = out
         del ham, phi, a, b, p, px
         torch.cuda.empty_cache()
+        return out
 
     def nerr(x, y):
         return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
 
-    r64, r32 = res[g.GQT_FP64], res[g.GQT_FP32_ACC64]
-    tab = {k: nerr(r32[k], r64[k]) for k in ("dos_mu", "vac_mu", "msd_mu", "dos", "vac", "msd", "sigma_vac",
-                                             "sigma_msd")}
-    return {"workload": f"honeycomb{L1}x{L1}_vac1pct_R{R}_M{M}", "steps": Nt, "errors_fp32_vs_fp64": tab,
-            "vac_seconds_fp64": r64["t_vac"], "vac_seconds_fp32": r32["t_vac"],
-            "vac_speedup_fp32": r64["t_vac"] / r32["t_vac"]}
+    r32 = run(g.GQT_FP32_ACC64, R, 0)
+    refs = [run(g.GQT_FP64, 1, r) for r in range(nref)]
+    tab = {}
+    for key, axis_r in (("dos_mu", 0), ("dos", 0)):
+        tab[key] = max(nerr(r32[key][r], refs[r][key][0]) for r in range(nref))
+    for key in ("vac_mu", "msd_mu"):
+        tab[key] = max(nerr(r32[key][k, r], refs[r][key][k, 0]) for r in range(nref) for k in range(r32[key].shape[0]))
+    for key in ("vac", "msd", "sigma_vac", "sigma_msd"):
+        tab[key] = max(nerr(r32[key][r], refs[r][key][0]) for r in range(nref))
+    marks = sorted({k for k in (0, 1, 2, 5, 10, 20, 50, 100, 150, Nt - 1) if k < Nt})
+    curve = {str(k): max(nerr(r32["vac_mu"][k, r], refs[r]["vac_mu"][k, 0]) for r in range(nref)) for k in marks}
+    sig_curve = {str(k): max(nerr(r32["sigma_vac"][r][k], refs[r]["sigma_vac"][0][k]) for r in range(nref))
+                 for k in marks if k > 0}
+    n = r32["n"]
+    v32 = n * R * M * Nt / r32["t_vac"]
+    t64 = float(np.mean([x["t_vac"] for x in refs]))
+    v64 = n * M * Nt / t64
+    return {"workload": f"honeycomb{L1}x{L1}_vac1pct_R{R}_M{M}", "vac_steps": Nt, "msd_steps": Nm,
+            "reference": f"FP64 handle, R = 1 rows (paired-FP32 moment arithmetic, FP64 evolution), vectors 0..{nref - 1}",
+            "errors_fp32_vs_fp64": tab, "vac_row_error_by_step": curve, "sigma_vac_error_by_step": sig_curve,
+            "vac_seconds_fp32_R%d" % R: r32["t_vac"], "vac_seconds_fp64_per_vector": t64,
+            "vac_orbital_moments_per_s_fp32": v32, "vac_orbital_moments_per_s_fp64": v64,
+            "vac_speedup_fp32": v32 / v64}
 
 
 def latency(args, g, torch):
@@ -774,13 +806,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-fp32", action="store_true", help="skip the batched FP32 vs FP64 comparison")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
-    ap.add_argument("--fp32-moments", type=int, default=512, help="moments of the FP32/FP64 comparison")
+    ap.add_argument("--fp32-moments", type=int, default=2048, help="moments of the FP32/FP64 comparison")
     ap.add_argument("--fp32-L", type=int, default=0, help="cubic L of the FP32 comparison (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="run only the FP32/FP64 comparison (profiling)")
     ap.add_argument("--precision", action="store_true", help="FP32 vs FP64 per-result error table (C4 workload)")
     ap.add_argument("--latency", action="store_true", help="latency-bound workloads (C1 graphs on/off, C5 gradient)")
     ap.add_argument("--paper-examples", action="store_true", help="the paper's two examples (Sec. 5), timed")
-    ap.add_argument("--precision-steps", type=int, default=3, help="VAC/MSD time steps of the error table")
+    ap.add_argument("--precision-steps", type=int, default=200, help="VAC time steps of the error table")
+    ap.add_argument("--precision-msd-steps", type=int, default=3, help="MSD time steps of the error table")
+    ap.add_argument("--precision-ref-vectors", type=int, default=2, help="FP64 reference vectors of the error table")
     ap.add_argument("--hall", action="store_true", help="Hall conductivity (Kubo-Bastin) of the Haldane model")
     ap.add_argument("--hall-L", type=int, default=0, help="Haldane cells per side of the Hall run (profiling)")
     ap.add_argument("--hall-moments", type=int, default=0, help="Kubo-Bastin moments of the Hall run (profiling)")

@@ -364,6 +364,23 @@ gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
  * R > 1 rows, always use the FP64 pipe. */
 gqt_status gqt_set_fp64_arith(gqt_ham* ham, int mode);
 
+/* Temporal blocking of the paired-FP32 rows (default 0): on handles whose
+ * neighbour lists follow the honeycomb cell layout of the built-in lattice (site
+ * 2(c1 + L1 c2) + s, A(c1,c2) bonded to B(c1,c2), B(c1+1,c2-1), B(c1,c2-1), one
+ * slot order per sublattice, every row with three neighbours; recognised when the
+ * handle is built, vacancies included) with L1 and L2 multiples of 16 and
+ * one segment, each launch advances the rows by two Chebyshev steps over tiles of
+ * 16 x 16 cells: T_m on the tile plus a two-cell halo in shared memory, T_{m+1}
+ * on the tile plus a one-cell halo (recomputed by neighbouring tiles), T_{m+2}
+ * on the tile.  Per two steps each orbital's vectors and hoppings are read once
+ * and the index array not at all.  Results agree with the single-step kernels
+ * to rounding.  The handle holds two more vectors per chain.  0 = one step per
+ * launch.  Measured on GB300 (honeycomb 4096 x 2048): DRAM bytes per two steps
+ * 151 per orbital instead of 280 for the VAC rows, but the launch is bound by
+ * its instruction issue (halo recomputation, staging), 681 us against 2 x 340 us,
+ * so it is off by default. */
+gqt_status gqt_set_temporal_blocking(gqt_ham* ham, int enable);
+
 /* Blocked sweep order of the multi-vector kernels (default 1; built-in simple-
  * cubic lattices whose side is a power of two >= 64): the CTAs walk the x-rows in
  * strips of 32 y-rows through all z before the next strip, so the +-z neighbour
@@ -384,7 +401,9 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
  * 5 = moment steps m >= 2 with l = r (two moments per step), 6 = moment steps
  * m >= 2 of the two-recurrence l != r rows (two moments per step), 7 = Hall
  * chain orders (gqt_kb_moments), 8 = Hall moment contraction (the M x M
- * complex GEMM), 9 = Kubo-Bastin energy sums (gqt_kubo_bastin).  Graph
+ * complex GEMM), 9 = Kubo-Bastin energy sums (gqt_kubo_bastin), 10 =
+ * temporally blocked passes of the two-recurrence rows (two steps, four moments
+ * per launch), 11 = temporally blocked passes of the l = r rows.  Graph
  * capture is bypassed while profiling. */
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);

@@ -60,6 +60,7 @@ _SIGS = {
     "gqt_set_kb_contraction": [_P, _I],
     "gqt_set_wait_limit": [_P, _I],
     "gqt_set_fp64_arith": [_P, _I],
+    "gqt_set_temporal_blocking": [_P, _I],
     "gqt_kubo_bastin": [_P, _I, _P, _I, _D, _D, _I, _P, _P],
     "gqt_kubo_bastin_fermi": [_P, _I, _P, _I, _D, _D, _I, _P, _I, _D, _P, _P],
     "gqt_sigma_vac_loss_weights": [_I, _P, _I, _P, _D, _D, _I, _P, _I, _P, _P],
@@ -357,6 +358,12 @@ def gqt_set_fp64_arith(ham: Ham, mode: int):
     """Moment rows of an FP64 handle with one vector: 1 = pairs of FP32 numbers on the
     FP32 pipes (default), 0 = FP64 fused multiply-adds."""
     _check(lib().gqt_set_fp64_arith(ham.ptr, int(mode)))
+
+
+def gqt_set_temporal_blocking(ham: Ham, enable: bool):
+    """Two Chebyshev steps per launch over tiles of honeycomb cells (paired-FP32 rows of
+    honeycomb-layout handles; default off)."""
+    _check(lib().gqt_set_temporal_blocking(ham.ptr, int(bool(enable))))
 
 
 def gqt_set_wait_limit(ham: Ham, polls: int):

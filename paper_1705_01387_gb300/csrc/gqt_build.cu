@@ -264,6 +264,55 @@ gqt_ham::~gqt_ham() {
     if (e) cudaEventDestroy(e);
 }
 
+// The honeycomb cell layout of the built-in lattice (site 2(c1 + L1 c2) + s;
+// A(c1,c2) bonds to B(c1,c2), B(c1+1,c2-1), B(c1,c2-1) -- neighbour types 0, 1,
+// 2 -- and B to the mirror images), recognised from the neighbour list alone:
+// every row lists its three neighbours, in one slot order per sublattice.  This
+// holds for the built-in honeycomb lattices and for the same lattice given in the
+// paper's input form; vacancies (bonds with zero hopping) keep their indices.
+// Returns L1 and fills type[s][k] (the neighbour type of slot k on sublattice
+// s), or 0 when the rows do not follow the layout.
+static int64_t detect_honeycomb(const HostModel& m, int (&type)[2][3]) {
+  if (m.K != 3 || m.n < 18 || (m.n & 1)) return 0;
+  for (int64_t i = 0; i < m.n; ++i)
+    if (m.cnt[i] != 3) return 0;
+  const int64_t nc = m.n / 2;
+  for (int64_t L1 = 3; L1 * 3 <= nc; ++L1) {
+    if (nc % L1) continue;
+    const int64_t L2 = nc / L1;
+    auto nbr = [&](int64_t i, int t) -> int64_t {
+      const int64_t c = i >> 1, c1 = c % L1, c2 = c / L1;
+      const int s = (int)(i & 1);
+      const int64_t d1 = (t == 1) ? (s ? -1 : 1) : 0, d2 = (t == 0) ? 0 : (s ? 1 : -1);
+      const int64_t e1 = (c1 + d1 + L1) % L1, e2 = (c2 + d2 + L2) % L2;
+      return 2 * (e1 + L1 * e2) + (1 - s);
+    };
+    int ty[2][3];
+    bool ok = true;
+    for (int s = 0; s < 2 && ok; ++s) {
+      bool used[3] = {false, false, false};
+      for (int k = 0; k < 3 && ok; ++k) {
+        ty[s][k] = -1;
+        for (int t = 0; t < 3; ++t)
+          if (!used[t] && nbr(s, t) == m.idx[s * 3 + k]) {
+            ty[s][k] = t;
+            used[t] = true;
+            break;
+          }
+        ok = ty[s][k] >= 0;
+      }
+    }
+    for (int64_t i = 0; i < m.n && ok; ++i)
+      for (int k = 0; k < 3 && ok; ++k) ok = nbr(i, ty[i & 1][k]) == m.idx[i * 3 + k];
+    if (ok) {
+      for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 3; ++k) type[s][k] = ty[s][k];
+      return L1;
+    }
+  }
+  return 0;
+}
+
 extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double energy_scale, gqt_precision precision,
                                             const int64_t* seg_offsets, int nseg, gqt_ham** out) {
   gqt::NvtxRange nvtx_call_(__func__);
@@ -395,6 +444,10 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
       int sh = 0;
       while ((int64_t(1) << sh) < L) ++sh;
       if (L >= 64 && (int64_t(1) << sh) == L) h->row_shift = sh;
+    }
+    if (nseg == 1) {
+      h->honey_L1 = (int)detect_honeycomb(m, h->honey_type);
+      h->honey_L2 = h->honey_L1 > 0 ? (int)(m.n / 2 / h->honey_L1) : 0;
     }
     h->d_flag.ensure(16);
     check_cuda(cudaMemset(h->d_flag.p, 0, 16), "memset");

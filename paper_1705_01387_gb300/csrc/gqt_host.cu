@@ -26,6 +26,7 @@
 #include "gqt_kernels.cuh"
 #include "gqt_cluster.cuh"
 #include "gqt_df.cuh"
+#include "gqt_tile.cuh"
 
 using namespace gqt;
 
@@ -751,36 +752,99 @@ static int df_occupancy(int K, bool pair, int threads) {
   }
 }
 
+// Temporal blocking of the paired-FP32 rows (two orders per pass, gqt_tile.cuh):
+// honeycomb handles whose rows follow the built-in cell layout, one segment,
+// cell counts that the tiles divide.
+static bool tiled_applies(const gqt_ham* h) {
+  return h->use_tiling && h->honey_L1 > 0 && h->nseg == 1 && h->K == 3 && h->honey_L1 % TL_TX == 0 &&
+         h->honey_L2 % TL_TY == 0;
+}
+
+static Honey honey_of(const gqt_ham* h) {
+  Honey G;
+  G.L1 = h->honey_L1;
+  G.L2 = h->honey_L2;
+  // cell offsets of the three neighbour types, A (s = 0) and B (s = 1)
+  static const int O1[2][3] = {{0, 1, 0}, {0, -1, 0}}, O2[2][3] = {{0, -1, -1}, {0, 1, 1}};
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 3; ++k) {
+      G.o1[s][k] = O1[s][h->honey_type[s][k]];
+      G.o2[s][k] = O2[s][h->honey_type[s][k]];
+    }
+  return G;
+}
+
+template <bool CH, int NC>
+static int tiled_grid(int nb) {
+  int n = 0;
+  const size_t smem = TileSmem<CH, NC>::bytes;
+  if (cudaFuncSetAttribute(k_cheb2_honey_df<CH, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cheb2_honey_df<CH, NC>, tl_threads<NC>(), smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return std::max(1, std::min(std::max(n, 1) * sm_count(), nb));
+}
+
+// The rows' chains live in rotating buffers (4 per chain when tiled, else 2):
+// after step j, T_j is in buffer cur and T_{j-1} in buffer prv.  A single-order
+// step writes T_{j+1} over T_{j-1} (same element, same thread); a tiled pass
+// reads T_j and T_{j-1} and writes T_{j+1} and T_{j+2} into the two other buffers.
 template <bool CH, int KK>
 static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const void* l, const void* r,
-                    float4* A1, float4* A2, float4* W1, float4* W2, double2* partial, cudaStream_t s2) {
+                    float4* const* A, float4* const* B, int tgrid, double2* partial, cudaStream_t s2) {
+  const bool tiled = tgrid > 0;
   const DfEll<CH> H = df_ell_of<CH>(h);
   const int4* tab = (const int4*)T.d_tab4.p;
   const int nb = T.nblocks;
   const size_t sm = smem_bytes(h, 1, 3);
-  for (int m = 1; m <= std::max(steps, 1); ++m) {
-    float4* aout = (m % 2 == 1) ? A1 : A2;
-    float4* bout = (m % 2 == 1) ? W1 : W2;
+  int cur = 0, prv = 1;
+  for (int m = 1; m <= std::max(steps, 1);) {
     size_t pe = prof_begin(s2);
-    if (pair) {
-      if (m == 1)
-        k_cheb_pair_df<CH, KK, true><<<nb, h->threads, sm, s2>>>(H, tab, l, r, nullptr, nullptr, aout, bout, A2, W2,
-                                                                 partial, nb, m, 2 * steps);
+    if (m == 1) {
+      if (pair)
+        k_cheb_pair_df<CH, KK, true><<<nb, h->threads, sm, s2>>>(H, tab, l, r, nullptr, nullptr, A[0], B[0], A[1],
+                                                                 B[1], partial, nb, 1, 2 * steps);
       else
-        k_cheb_pair_df<CH, KK, false><<<nb, h->threads, sm, s2>>>(H, tab, (m - 1) % 2 == 1 ? A1 : A2,
-                                                                  (m - 1) % 2 == 1 ? W1 : W2, aout, bout, aout, bout,
-                                                                  nullptr, nullptr, partial, nb, m, 2 * steps);
-      check_launch("k_cheb_pair_df");
-      prof_end(pe, m == 1 ? 0 : 6, s2);
-    } else {
-      if (m == 1)
-        k_cheb_dbl_df<CH, KK, df_u(KK), true><<<nb, h->threads, sm, s2>>>(H, tab, r, nullptr, bout, W2, partial, nb, m);
-      else
-        k_cheb_dbl_df<CH, KK, df_u(KK), false><<<nb, h->threads, sm, s2>>>(H, tab, (m - 1) % 2 == 1 ? W1 : W2, bout, bout,
-                                                                       nullptr, partial, nb, m);
-      check_launch("k_cheb_dbl_df");
-      prof_end(pe, m == 1 ? 0 : 5, s2);
+        k_cheb_dbl_df<CH, KK, df_u(KK), true><<<nb, h->threads, sm, s2>>>(H, tab, r, nullptr, B[0], B[1], partial, nb,
+                                                                          1);
+      check_launch(pair ? "k_cheb_pair_df(first)" : "k_cheb_dbl_df(first)");
+      prof_end(pe, 0, s2);
+      m = 2;
+      continue;
     }
+    if constexpr (KK == 3) {
+      if (tiled && m + 1 <= steps) {
+        int f[2], nf = 0;
+        for (int b = 0; b < 4 && nf < 2; ++b)
+          if (b != cur && b != prv) f[nf++] = b;
+        const Honey G = honey_of(h);
+        const size_t tsm = pair ? TileSmem<CH, 2>::bytes : TileSmem<CH, 1>::bytes;
+        if (pair)
+          k_cheb2_honey_df<CH, 2><<<tgrid, tl_threads<2>(), tsm, s2>>>(
+              H, G, A[cur], A[prv], B[cur], B[prv], A[f[0]], A[f[1]], B[f[0]], B[f[1]], partial, nb, 2 * m - 2);
+        else
+          k_cheb2_honey_df<CH, 1><<<tgrid, tl_threads<1>(), tsm, s2>>>(
+              H, G, B[cur], B[prv], nullptr, nullptr, B[f[0]], B[f[1]], nullptr, nullptr, partial, nb, 2 * m - 2);
+        check_launch("k_cheb2_honey_df");
+        prof_end(pe, pair ? 10 : 11, s2);
+        prv = f[0];
+        cur = f[1];
+        m += 2;
+        continue;
+      }
+    }
+    if (pair)
+      k_cheb_pair_df<CH, KK, false><<<nb, h->threads, sm, s2>>>(H, tab, A[cur], B[cur], A[prv], B[prv], A[prv],
+                                                                B[prv], nullptr, nullptr, partial, nb, m, 2 * steps);
+    else
+      k_cheb_dbl_df<CH, KK, df_u(KK), false><<<nb, h->threads, sm, s2>>>(H, tab, B[cur], B[prv], B[prv], nullptr,
+                                                                         partial, nb, m);
+    check_launch(pair ? "k_cheb_pair_df" : "k_cheb_dbl_df");
+    prof_end(pe, pair ? 6 : 5, s2);
+    std::swap(cur, prv);
+    ++m;
   }
 }
 
@@ -796,26 +860,43 @@ static void launch_moments_df(gqt_ham* h, const void* l, const void* r, int M, v
   const BlockTable& T = h->table(1, occ);
   const int nb = T.nblocks;
   const size_t vb = h->vec_bytes(1);
-  float4* W1 = (float4*)h->ws(WS_T1, vb).p;
-  float4* W2 = (float4*)h->ws(WS_T2, vb).p;
-  float4* A1 = pair ? (float4*)h->ws(WS_PA1, vb).p : nullptr;
-  float4* A2 = pair ? (float4*)h->ws(WS_PA2, vb).p : nullptr;
-  const int slots = std::max(M, 2) + 2;
+  const bool tiled = tiled_applies(h);
+  float4* A[4] = {nullptr, nullptr, nullptr, nullptr};
+  float4* B[4] = {(float4*)h->ws(WS_T1, vb).p, (float4*)h->ws(WS_T2, vb).p, nullptr, nullptr};
+  if (pair) {
+    A[0] = (float4*)h->ws(WS_PA1, vb).p;
+    A[1] = (float4*)h->ws(WS_PA2, vb).p;
+  }
+  if (tiled) {
+    B[2] = (float4*)h->ws(WS_TILE0, vb).p;
+    B[3] = (float4*)h->ws(WS_TILE0 + 1, vb).p;
+    if (pair) {
+      A[2] = (float4*)h->ws(WS_TILE0 + 2, vb).p;
+      A[3] = (float4*)h->ws(WS_TILE0 + 3, vb).p;
+    }
+  }
+  const int slots = std::max(M, 2) + 4;
   double2* partial = (double2*)h->ws(WS_PARTIAL, (size_t)slots * std::max(nb, 16) * sizeof(double2)).p;
   const int steps = (M + 1) / 2;
   const double tol = 1e-6;
   const size_t total = (size_t)h->nseg * M;
   const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
-  const std::string key = key_of("momdf", {l, r, out, W1, W2, A1, A2, partial, T.d_blk.p},
-                                 {(double)kind, (double)M, (double)h->threads, (double)nb});
+  // grid of the tiled passes: their resident CTAs (set before any capture)
+  int tgrid = 0;
+  if (tiled)
+    tgrid = pair ? (h->hop_real ? tiled_grid<false, 2>(nb) : tiled_grid<true, 2>(nb))
+                 : (h->hop_real ? tiled_grid<false, 1>(nb) : tiled_grid<true, 1>(nb));
+  const std::string key = key_of("momdf", {l, r, out, A[0], A[1], A[2], A[3], B[0], B[1], B[2], B[3], partial,
+                                           T.d_blk.p},
+                                 {(double)kind, (double)M, (double)h->threads, (double)nb, (double)tgrid});
   run_graph(h, key, st, [&](cudaStream_t s2) {
     auto rows = [&](auto ch) {
       constexpr bool CH = decltype(ch)::value;
       switch (h->K) {
-        case 2: df_rows<CH, 2>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
-        case 3: df_rows<CH, 3>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
-        case 4: df_rows<CH, 4>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
-        default: df_rows<CH, 6>(h, T, pair, steps, l, r, A1, A2, W1, W2, partial, s2); break;
+        case 2: df_rows<CH, 2>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
+        case 3: df_rows<CH, 3>(h, T, pair, steps, l, r, A, B, tgrid, partial, s2); break;
+        case 4: df_rows<CH, 4>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
+        default: df_rows<CH, 6>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
       }
     };
     if (h->hop_real)
@@ -1284,6 +1365,13 @@ gqt_status gqt_set_vac_pair(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_pair = enable != 0;
+  API_END
+}
+
+gqt_status gqt_set_temporal_blocking(gqt_ham* h, int enable) {
+  API_BEGIN
+  require(h != nullptr, "null handle");
+  h->use_tiling = enable != 0;
   API_END
 }
 

@@ -75,7 +75,8 @@ enum WorkSlot {
   WS_PA1 = 18,  // chain A buffers of the two-recurrence (pair) moment rows
   WS_PA2 = 19,
   WS_ADJ0 = 20,  // adjoint workspace slots start here
-  WS_STAGE0 = 96  // +0, +1: host-resident VAC/MSD state staged on the device
+  WS_STAGE0 = 96,  // +0, +1: host-resident VAC/MSD state staged on the device
+  WS_TILE0 = 98    // +0..+3: the third and fourth chain buffers of the tiled rows
 };
 
 uint64_t splitmix_mix(uint64_t z);
@@ -113,6 +114,12 @@ struct gqt_ham {
   int fp64_arith = 1;       // FP64 handles' R = 1 moment rows: 0 FP64 pipe, 1 pairs of FP32 (gqt_set_fp64_arith)
   gqt::DevBuf d_hop_df, d_diag_df;  // 2H~ and 2U/dE as (hi, lo) FP32 pairs, split on first use
   bool df_ready = false;
+  // honeycomb cell layout recognised at build (site 2(c1 + L1 c2) + s; 0 = not that
+  // layout) and, per sublattice and ELL slot, the neighbour type; enables the
+  // temporally blocked rows (gqt_set_temporal_blocking)
+  int honey_L1 = 0, honey_L2 = 0;
+  int honey_type[2][3] = {{0, 1, 2}, {0, 1, 2}};
+  bool use_tiling = false;
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

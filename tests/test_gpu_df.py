@@ -172,3 +172,76 @@ def test_df_full_size_agrees_with_fp64_mode():
     for k in range(3):
         assert nerr(rows[1][k], rows[0][k]) < 1e-12, k
     assert abs(rows[1][0][0] - 1.0) < 1e-13
+
+
+def _tiled_launches(fn):
+    g.gqt_profile_start()
+    fn()
+    torch.cuda.synchronize()
+    _, n = g.gqt_profile_stop(12)
+    return int(n[10] + n[11])
+
+
+TILED = {
+    "honeycomb64x32": lambda: (S.honeycomb(64, 32, -2.7, 2.0, seed=13), S.energy_scale_rule(3, -2.7, 2.0)),
+    "honeycomb96x48_vac": lambda: (S.honeycomb(96, 48, -2.7, 0.5, seed=14, vacancy_frac=0.01),
+                                   S.energy_scale_rule(3, -2.7, 0.5)),
+    "honeycomb64x32_phases": lambda: (S.with_random_bond_phases(S.honeycomb(64, 32, -2.7, 2.0, seed=15), 16),
+                                      S.energy_scale_rule(3, -2.7, 2.0)),
+}
+
+
+@pytest.mark.parametrize("name", list(TILED))
+@pytest.mark.parametrize("M", [1, 3, 4, 5, 6, 9, 130, 257])
+def test_tiled_rows_match_oracle_and_single_step(name, M):
+    """Temporal blocking (two steps per launch over 32 x 16-cell tiles with a
+    recomputed halo) on honeycomb lattices whose cell counts the tiles divide,
+    with disorder, vacancies and complex hoppings, for step counts that leave
+    0 or 1 single steps after the blocked passes: DOS, VAC and MSD rows within
+    1e-10 of the oracle and within 1e-13 of the single-step kernels, and the
+    blocked kernel must actually have run."""
+    lat, dE = TILED[name]()
+    h = O.Hamiltonian(lat, dE)
+    phi = S.random_phase(lat.n, 1, seed=M + 1)
+    d = torch.from_numpy(phi).cuda()
+    dts = np.array([0.5])
+    Np = [O.np_rule(dE * 0.5, 64)]
+    rows = {}
+    for tiling in (True, False):
+        ham = _ham(lat, dE)
+        g.gqt_set_temporal_blocking(ham, tiling)
+        dos = np.empty((1, 1, M))
+        vac = np.empty((1, 1, 1, M))
+        msd = np.empty((1, 1, 1, M))
+        a, b, p, px = (torch.empty_like(d) for _ in range(4))
+        g.gqt_vac_init(ham, d, a, b, 1)
+        g.gqt_msd_init(ham, d, p, px, 1)
+
+        def run():
+            g.gqt_dos_moments(ham, d, 1, M, dos)
+            g.gqt_vac_moments(ham, a, b, 1, dts, M, vac, Np=Np)
+            g.gqt_msd_moments(ham, p, px, 1, dts, M, msd, Np=Np)
+
+        n_tiled = _tiled_launches(run)
+        steps = (M + 1) // 2
+        assert (n_tiled > 0) == (tiling and steps >= 3), n_tiled
+        rows[tiling] = (dos.ravel(), vac.ravel(), msd.ravel())
+    ref = (h.dos_moments(phi[:, 0], M).real, h.vac_moments(phi[:, 0], dts, Np, M)[0],
+           h.msd_moments(phi[:, 0], dts, Np, M)[0])
+    for k in range(3):
+        assert nerr(rows[True][k], ref[k]) < TOL64, k
+        assert nerr(rows[True][k], rows[False][k]) < 1e-13, k
+
+
+def test_tiled_layout_not_recognised_falls_back():
+    """A honeycomb lattice whose cells the tiles do not divide (40 x 24), and a square
+    lattice, run the single-step kernels (no blocked launch) and stay exact."""
+    for lat, dE in ((S.honeycomb(40, 24, -2.7, 2.0, seed=16), S.energy_scale_rule(3, -2.7, 2.0)),
+                    (S.square(41, 29, -1.0, 4.0, seed=5), S.energy_scale_rule(4, -1.0, 4.0))):
+        ham = _ham(lat, dE)
+        phi = S.random_phase(lat.n, 1, seed=3)
+        d = torch.from_numpy(phi).cuda()
+        g.gqt_set_temporal_blocking(ham, True)
+        mu = np.empty((1, 1, 64))
+        assert _tiled_launches(lambda: g.gqt_dos_moments(ham, d, 1, 64, mu)) == 0
+        assert nerr(mu.ravel(), O.Hamiltonian(lat, dE).dos_moments(phi[:, 0], 64).real) < TOL64
