@@ -247,7 +247,10 @@ gqt_status gqt_set_kb_contraction(gqt_ham* ham, int mode);
  * runs out stops the pipeline; the thread then drains what is in flight (the
  * last committed products and the issued copies, 2^24 polls each, independent of
  * this setting), frees its tensor memory and the call returns GQT_ETIMEOUT; the
- * moments it wrote are not valid.  The handle stays usable.  This is the library's failure
+ * moments it wrote are not valid.  The handle stays usable.  If the drain
+ * itself gives up (the error message then says so), products or copies may still
+ * be in flight when the CTA frees its tensor memory and exits: treat the CUDA
+ * context as suspect and restart the process.  This is the library's failure
  * detection for a device wait that never completes (Sec. 4.2 names a too-small
  * energy scale as the method's failure mode; a stalled copy engine is the
  * hardware's).  polls < 0: GQT_EINVAL. */
@@ -364,21 +367,22 @@ gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
  * R > 1 rows, always use the FP64 pipe. */
 gqt_status gqt_set_fp64_arith(gqt_ham* ham, int mode);
 
-/* Temporal blocking of the paired-FP32 rows (default 0): on handles whose
- * neighbour lists follow the honeycomb cell layout of the built-in lattice (site
- * 2(c1 + L1 c2) + s, A(c1,c2) bonded to B(c1,c2), B(c1+1,c2-1), B(c1,c2-1), one
- * slot order per sublattice, every row with three neighbours; recognised when the
- * handle is built, vacancies included) with L1 and L2 multiples of 16 and
- * one segment, each launch advances the rows by two Chebyshev steps over tiles of
- * 16 x 16 cells: T_m on the tile plus a two-cell halo in shared memory, T_{m+1}
- * on the tile plus a one-cell halo (recomputed by neighbouring tiles), T_{m+2}
- * on the tile.  Per two steps each orbital's vectors and hoppings are read once
- * and the index array not at all.  Results agree with the single-step kernels
- * to rounding.  The handle holds two more vectors per chain.  0 = one step per
- * launch.  Measured on GB300 (honeycomb 4096 x 2048): DRAM bytes per two steps
- * 151 per orbital instead of 280 for the VAC rows, but the launch is bound by
- * its instruction issue (halo recomputation, staging), 681 us against 2 x 340 us,
- * so it is off by default. */
+/* Temporal blocking of the paired-FP32 rows (Eq. 21 advanced two orders per
+ * launch; default 1).  Applies to FP64 handles in paired-FP32 mode with R = 1
+ * whose neighbour lists follow the honeycomb cell layout of the built-in
+ * lattice (site 2(c1 + L1 c2) + s, A(c1,c2) bonded to B(c1,c2), B(c1+1,c2-1),
+ * B(c1,c2-1), one slot order per sublattice, every row with three neighbours;
+ * recognised when the handle is built, vacancies included), with L1 a multiple
+ * of 32 cells and one segment.  Each CTA walks a band of 128 (or 64, 32) cells
+ * down the rows: per row it computes T_{m+1} from T_m and T_{m-1}, and T_{m+2}
+ * two rows behind from the T_{m+1} rows it wrote just before (still in L2), so
+ * per two orders each orbital's vectors and hoppings come from DRAM once and
+ * the index array is not read (VAC rows 160 bytes per orbital instead of 280,
+ * l = r rows 96 instead of 184).  Each CTA recomputes the T_{m+1} values at its
+ * band's edges itself.  Results agree with the single-order kernels to
+ * rounding (the moment sums are split over CTAs differently).  The handle holds
+ * two more vectors per chain.  0 = one order per launch; other handles always
+ * run one order per launch. */
 gqt_status gqt_set_temporal_blocking(gqt_ham* ham, int enable);
 
 /* Blocked sweep order of the multi-vector kernels (default 1; built-in simple-

@@ -361,8 +361,8 @@ def gqt_set_fp64_arith(ham: Ham, mode: int):
 
 
 def gqt_set_temporal_blocking(ham: Ham, enable: bool):
-    """Two Chebyshev steps per launch over tiles of honeycomb cells (paired-FP32 rows of
-    honeycomb-layout handles; default off)."""
+    """Two Chebyshev orders per launch, each CTA walking a band of honeycomb cells
+    down the rows (paired-FP32 rows of honeycomb-layout handles; default on)."""
     _check(lib().gqt_set_temporal_blocking(ham.ptr, int(bool(enable))))
 
 

@@ -754,10 +754,10 @@ static int df_occupancy(int K, bool pair, int threads) {
 
 // Temporal blocking of the paired-FP32 rows (two orders per pass, gqt_tile.cuh):
 // honeycomb handles whose rows follow the built-in cell layout, one segment,
-// cell counts that the tiles divide.
+// L1 a multiple of 32 cells (the band width).
 static bool tiled_applies(const gqt_ham* h) {
-  return h->use_tiling && h->honey_L1 > 0 && h->nseg == 1 && h->K == 3 && h->honey_L1 % TL_TX == 0 &&
-         h->honey_L2 % TL_TY == 0;
+  return h->use_tiling && h->honey_L1 > 0 && h->nseg == 1 && h->K == 3 && tl_band_width(h->honey_L1) > 0 &&
+         h->honey_L2 >= 2;
 }
 
 static Honey honey_of(const gqt_ham* h) {
@@ -774,17 +774,20 @@ static Honey honey_of(const gqt_ham* h) {
   return G;
 }
 
+
+// CTAs of the blocked kernel: as many as are resident at once (each takes an
+// equal share of the band rows), at most the single-order grid nb (the stride of
+// the moment partial slots).
+constexpr size_t TL_SMEM = 4 * 8 * sizeof(double);  // block_reduce_rx<4> over at most 8 warps
+
 template <bool CH, int NC>
-static int tiled_grid(int nb) {
+static int tiled_grid(int threads) {
   int n = 0;
-  const size_t smem = TileSmem<CH, NC>::bytes;
-  if (cudaFuncSetAttribute(k_cheb2_honey_df<CH, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cheb2_honey_df<CH, NC>, tl_threads<NC>(), smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cheb2_honey_df<CH, NC>, threads, TL_SMEM) != cudaSuccess) {
     cudaGetLastError();
     n = 1;
   }
-  return std::max(1, std::min(std::max(n, 1) * sm_count(), nb));
+  return std::max(1, n) * sm_count();
 }
 
 // The rows' chains live in rotating buffers (4 per chain when tiled, else 2):
@@ -793,7 +796,8 @@ static int tiled_grid(int nb) {
 // reads T_j and T_{j-1} and writes T_{j+1} and T_{j+2} into the two other buffers.
 template <bool CH, int KK>
 static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const void* l, const void* r,
-                    float4* const* A, float4* const* B, int tgrid, double2* partial, cudaStream_t s2) {
+                    float4* const* A, float4* const* B, int tgrid, int tnseg, double2* partial,
+                    double2* tscratch, cudaStream_t s2) {
   const bool tiled = tgrid > 0;
   const DfEll<CH> H = df_ell_of<CH>(h);
   const int4* tab = (const int4*)T.d_tab4.p;
@@ -820,14 +824,25 @@ static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const
         for (int b = 0; b < 4 && nf < 2; ++b)
           if (b != cur && b != prv) f[nf++] = b;
         const Honey G = honey_of(h);
-        const size_t tsm = pair ? TileSmem<CH, 2>::bytes : TileSmem<CH, 1>::bytes;
+        const int bw = tl_band_width(G.L1);
+        // partial dots: straight into the moment slots when the grid fits them, else
+        // per CTA into scratch and folded
+        const bool fold = tgrid > nb;
+        double2* pout = fold ? tscratch : partial + (size_t)(2 * m - 2) * nb;
+        const int ostride = fold ? tgrid : nb, nzero = fold ? 0 : nb;
         if (pair)
-          k_cheb2_honey_df<CH, 2><<<tgrid, tl_threads<2>(), tsm, s2>>>(
-              H, G, A[cur], A[prv], B[cur], B[prv], A[f[0]], A[f[1]], B[f[0]], B[f[1]], partial, nb, 2 * m - 2);
+          k_cheb2_honey_df<CH, 2><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, A[cur], A[prv], B[cur], B[prv],
+                                                                 A[f[0]], A[f[1]], B[f[0]], B[f[1]], pout, ostride,
+                                                                 nzero);
         else
-          k_cheb2_honey_df<CH, 1><<<tgrid, tl_threads<1>(), tsm, s2>>>(
-              H, G, B[cur], B[prv], nullptr, nullptr, B[f[0]], B[f[1]], nullptr, nullptr, partial, nb, 2 * m - 2);
+          k_cheb2_honey_df<CH, 1><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, B[cur], B[prv], nullptr, nullptr,
+                                                                 B[f[0]], B[f[1]], nullptr, nullptr, pout, ostride,
+                                                                 nzero);
         check_launch("k_cheb2_honey_df");
+        if (fold) {
+          k_tl_fold<<<4, 128, 0, s2>>>(tscratch, tgrid, partial, nb, 2 * m - 2);
+          check_launch("k_tl_fold");
+        }
         prof_end(pe, pair ? 10 : 11, s2);
         prv = f[0];
         cur = f[1];
@@ -882,21 +897,33 @@ static void launch_moments_df(gqt_ham* h, const void* l, const void* r, int M, v
   const size_t total = (size_t)h->nseg * M;
   const int rb = (int)std::min<size_t>((total + 255) / 256, 4096);
   // grid of the tiled passes: their resident CTAs (set before any capture)
-  int tgrid = 0;
-  if (tiled)
-    tgrid = pair ? (h->hop_real ? tiled_grid<false, 2>(nb) : tiled_grid<true, 2>(nb))
-                 : (h->hop_real ? tiled_grid<false, 1>(nb) : tiled_grid<true, 1>(nb));
+  int tgrid = 0, tnseg = 0;
+  double2* tscratch = nullptr;
+  if (tiled) {
+    // one CTA per band and segment, the segments as many as the resident CTAs allow
+    // (the CTAs of a segment then walk its rows across all bands together)
+    const int bw = tl_band_width(h->honey_L1), thr = 2 * bw, nbands = h->honey_L1 / bw;
+    const int res = pair ? (h->hop_real ? tiled_grid<false, 2>(thr) : tiled_grid<true, 2>(thr))
+                         : (h->hop_real ? tiled_grid<false, 1>(thr) : tiled_grid<true, 1>(thr));
+    if (nbands <= res) {
+      tnseg = res / nbands;
+      tgrid = nbands * tnseg;
+    } else {
+      tgrid = res;  // more bands than resident CTAs: equal ranges of band rows
+    }
+    if (tgrid > nb) tscratch = (double2*)h->ws(WS_TILE_SCRATCH, (size_t)4 * tgrid * sizeof(double2)).p;
+  }
   const std::string key = key_of("momdf", {l, r, out, A[0], A[1], A[2], A[3], B[0], B[1], B[2], B[3], partial,
-                                           T.d_blk.p},
-                                 {(double)kind, (double)M, (double)h->threads, (double)nb, (double)tgrid});
+                                           T.d_blk.p, tscratch},
+                                 {(double)kind, (double)M, (double)h->threads, (double)nb, (double)tgrid, (double)tnseg});
   run_graph(h, key, st, [&](cudaStream_t s2) {
     auto rows = [&](auto ch) {
       constexpr bool CH = decltype(ch)::value;
       switch (h->K) {
-        case 2: df_rows<CH, 2>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
-        case 3: df_rows<CH, 3>(h, T, pair, steps, l, r, A, B, tgrid, partial, s2); break;
-        case 4: df_rows<CH, 4>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
-        default: df_rows<CH, 6>(h, T, pair, steps, l, r, A, B, 0, partial, s2); break;
+        case 2: df_rows<CH, 2>(h, T, pair, steps, l, r, A, B, 0, 0, partial, nullptr, s2); break;
+        case 3: df_rows<CH, 3>(h, T, pair, steps, l, r, A, B, tgrid, tnseg, partial, tscratch, s2); break;
+        case 4: df_rows<CH, 4>(h, T, pair, steps, l, r, A, B, 0, 0, partial, nullptr, s2); break;
+        default: df_rows<CH, 6>(h, T, pair, steps, l, r, A, B, 0, 0, partial, nullptr, s2); break;
       }
     };
     if (h->hop_real)

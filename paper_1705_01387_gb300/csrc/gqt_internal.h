@@ -76,7 +76,8 @@ enum WorkSlot {
   WS_PA2 = 19,
   WS_ADJ0 = 20,  // adjoint workspace slots start here
   WS_STAGE0 = 96,  // +0, +1: host-resident VAC/MSD state staged on the device
-  WS_TILE0 = 98    // +0..+3: the third and fourth chain buffers of the tiled rows
+  WS_TILE0 = 98,   // +0..+3: the third and fourth chain buffers of the tiled rows
+  WS_TILE_SCRATCH = 102  // per-CTA partial dots of a tiled grid larger than the single-order grid
 };
 
 uint64_t splitmix_mix(uint64_t z);
@@ -119,7 +120,7 @@ struct gqt_ham {
   // temporally blocked rows (gqt_set_temporal_blocking)
   int honey_L1 = 0, honey_L2 = 0;
   int honey_type[2][3] = {{0, 1, 2}, {0, 1, 2}};
-  bool use_tiling = false;
+  bool use_tiling = true;
   std::map<int, std::unique_ptr<gqt::BlockTable>> tables;
   std::vector<std::unique_ptr<gqt::DevBuf>> work;
   std::map<std::string, cudaGraphExec_t> graphs;

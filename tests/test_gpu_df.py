@@ -194,12 +194,12 @@ TILED = {
 @pytest.mark.parametrize("name", list(TILED))
 @pytest.mark.parametrize("M", [1, 3, 4, 5, 6, 9, 130, 257])
 def test_tiled_rows_match_oracle_and_single_step(name, M):
-    """Temporal blocking (two steps per launch over 32 x 16-cell tiles with a
-    recomputed halo) on honeycomb lattices whose cell counts the tiles divide,
-    with disorder, vacancies and complex hoppings, for step counts that leave
-    0 or 1 single steps after the blocked passes: DOS, VAC and MSD rows within
-    1e-10 of the oracle and within 1e-13 of the single-step kernels, and the
-    blocked kernel must actually have run."""
+    """Temporal blocking (two steps per launch, each CTA walking a band of cells
+    down the rows and recomputing its halo) on honeycomb lattices whose L1 the
+    bands divide, with disorder, vacancies and complex hoppings, for step counts
+    that leave 0 or 1 single steps after the blocked passes: DOS, VAC and MSD
+    rows within 1e-10 of the oracle and within 1e-13 of the single-step kernels,
+    and the blocked kernel must actually have run."""
     lat, dE = TILED[name]()
     h = O.Hamiltonian(lat, dE)
     phi = S.random_phase(lat.n, 1, seed=M + 1)
@@ -234,7 +234,7 @@ def test_tiled_rows_match_oracle_and_single_step(name, M):
 
 
 def test_tiled_layout_not_recognised_falls_back():
-    """A honeycomb lattice whose cells the tiles do not divide (40 x 24), and a square
+    """A honeycomb lattice whose L1 no band width divides (40 x 24), and a square
     lattice, run the single-step kernels (no blocked launch) and stay exact."""
     for lat, dE in ((S.honeycomb(40, 24, -2.7, 2.0, seed=16), S.energy_scale_rule(3, -2.7, 2.0)),
                     (S.square(41, 29, -1.0, 4.0, seed=5), S.energy_scale_rule(4, -1.0, 4.0))):
@@ -245,3 +245,57 @@ def test_tiled_layout_not_recognised_falls_back():
         mu = np.empty((1, 1, 64))
         assert _tiled_launches(lambda: g.gqt_dos_moments(ham, d, 1, 64, mu)) == 0
         assert nerr(mu.ravel(), O.Hamiltonian(lat, dE).dos_moments(phi[:, 0], 64).real) < TOL64
+
+
+BANDS = {
+    # one band of 32 cells: the halo wraps round the periodic boundary on both sides
+    "honeycomb32x4": (32, 4),
+    "honeycomb32x5": (32, 5),
+    # two segments, the second only two rows high
+    "honeycomb64x130": (64, 130),
+    # 32 bands x 8 segments (the last 104 rows): more work items than CTAs of the
+    # two-chain kernel, so a CTA carries its row rings from one item to the next
+    "honeycomb1024x1000": (1024, 1000),
+    # 64 bands x 5 segments (the last 8 rows): more items than CTAs of either kernel
+    "honeycomb2048x520": (2048, 520),
+}
+
+
+@pytest.mark.parametrize("name", list(BANDS))
+def test_tiled_band_geometry(name):
+    """Band walk of the blocked kernel at the edges of its geometry: a single band,
+    the fewest rows, ragged segments and several items per CTA.  Nine moments
+    (first order + two blocked passes) of DOS, VAC and MSD rows equal the
+    single-step kernels within 1e-13, and the DOS row the oracle within 1e-10."""
+    L1, L2 = BANDS[name]
+    lat = S.honeycomb(L1, L2, -2.7, 2.0, seed=L1 + L2, vacancy_frac=0.005)
+    dE = S.energy_scale_rule(3, -2.7, 2.0)
+    M = 9
+    phi = S.random_phase(lat.n, 1, seed=L2)
+    d = torch.from_numpy(phi).cuda()
+    dts = np.array([0.5])
+    Np = [O.np_rule(dE * 0.5, 64)]
+    rows = {}
+    for tiling in (True, False):
+        ham = _ham(lat, dE)
+        g.gqt_set_temporal_blocking(ham, tiling)
+        dos = np.empty((1, 1, M))
+        vac = np.empty((1, 1, 1, M))
+        msd = np.empty((1, 1, 1, M))
+        a, b, p, px = (torch.empty_like(d) for _ in range(4))
+        g.gqt_vac_init(ham, d, a, b, 1)
+        g.gqt_msd_init(ham, d, p, px, 1)
+
+        def run():
+            g.gqt_dos_moments(ham, d, 1, M, dos)
+            g.gqt_vac_moments(ham, a, b, 1, dts, M, vac, Np=Np)
+            g.gqt_msd_moments(ham, p, px, 1, dts, M, msd, Np=Np)
+
+        n_tiled = _tiled_launches(run)
+        assert (n_tiled > 0) == tiling, n_tiled
+        rows[tiling] = (dos.ravel(), vac.ravel(), msd.ravel())
+    for k in range(3):
+        assert nerr(rows[True][k], rows[False][k]) < 1e-13, k
+    ref = O.Hamiltonian(lat, dE).dos_moments(phi[:, 0], M).real
+    assert nerr(rows[True][0], ref) < TOL64
+
