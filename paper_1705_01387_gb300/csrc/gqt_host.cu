@@ -1381,10 +1381,19 @@ gqt_status gqt_set_graphs(gqt_ham* h, int enable) {
   API_END
 }
 
+// A setting that changes which kernels run, or their parameters, retires the
+// handle's captured graphs (their launches carry the old choice).
+static void drop_graphs(gqt_ham* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  h->graph_data.clear();
+}
+
 gqt_status gqt_set_cluster(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_cluster = enable != 0;
+  drop_graphs(h);
   API_END
 }
 
@@ -1392,6 +1401,7 @@ gqt_status gqt_set_vac_pair(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_pair = enable != 0;
+  drop_graphs(h);
   API_END
 }
 
@@ -1399,6 +1409,7 @@ gqt_status gqt_set_temporal_blocking(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_tiling = enable != 0;
+  drop_graphs(h);
   API_END
 }
 
@@ -1406,6 +1417,7 @@ gqt_status gqt_set_fp64_arith(gqt_ham* h, int mode) {
   API_BEGIN
   require(h != nullptr && (mode == 0 || mode == 1), "gqt_set_fp64_arith: mode must be 0 or 1");
   h->fp64_arith = mode;
+  drop_graphs(h);
   API_END
 }
 
@@ -1413,6 +1425,7 @@ gqt_status gqt_set_sweep_order(gqt_ham* h, int enable) {
   API_BEGIN
   require(h != nullptr, "null handle");
   h->use_sweep_order = enable != 0;
+  drop_graphs(h);
   API_END
 }
 

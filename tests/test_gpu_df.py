@@ -247,6 +247,25 @@ def test_tiled_layout_not_recognised_falls_back():
         assert nerr(mu.ravel(), O.Hamiltonian(lat, dE).dos_moments(phi[:, 0], 64).real) < TOL64
 
 
+def test_setting_change_retires_captured_graphs():
+    """Switching temporal blocking off and on again on one handle takes effect on
+    the next call although the call's pointers and sizes repeat (the captured
+    graphs that carried the old choice are retired): blocked launches run, then
+    none, then again, with the same moments to 1e-13."""
+    lat, dE = TILED["honeycomb64x32"]()
+    ham = _ham(lat, dE)
+    d = torch.from_numpy(S.random_phase(lat.n, 1, seed=4)).cuda()
+    M = 40
+    mus, counts = [], []
+    for tiling in (True, False, True):
+        g.gqt_set_temporal_blocking(ham, tiling)
+        mu = np.empty((1, 1, M))
+        counts.append(_tiled_launches(lambda: g.gqt_dos_moments(ham, d, 1, M, mu)))
+        mus.append(mu.ravel().copy())
+    assert counts[0] > 0 and counts[1] == 0 and counts[2] > 0, counts
+    assert nerr(mus[1], mus[0]) < 1e-13 and np.array_equal(mus[2], mus[0])
+
+
 BANDS = {
     # one band of 32 cells: the halo wraps round the periodic boundary on both sides
     "honeycomb32x4": (32, 4),
