@@ -265,6 +265,7 @@ def precision_table(args, g, torch):
     def run(prec, R_, first):
         ham = g.gqt_build_hamiltonian(None, dE, prec, kind=g.GQT_LATTICE_HONEYCOMB, L1=L1, L2=L1, t=-2.7, W=0.5,
                                       vacancy_frac=0.01, seed=w.seed)
+        g.gqt_set_temporal_blocking(ham, args.temporal_blocking)
         nO = ham.n / ham.volume
         cd = torch.complex128 if prec == g.GQT_FP64 else torch.complex64
         phi = torch.empty((ham.n, R_), dtype=cd, device="cuda")
@@ -333,7 +334,7 @@ def precision_table(args, g, torch):
             "errors_fp32_vs_fp64": tab, "vac_row_error_by_step": curve, "sigma_vac_error_by_step": sig_curve,
             "vac_seconds_fp32_R%d" % R: r32["t_vac"], "vac_seconds_fp64_per_vector": t64,
             "vac_orbital_moments_per_s_fp32": v32, "vac_orbital_moments_per_s_fp64": v64,
-            "vac_speedup_fp32": v32 / v64}
+            "vac_speedup_fp32": v32 / v64, "temporal_blocking": args.temporal_blocking}
 
 
 def latency(args, g, torch):

@@ -367,22 +367,26 @@ gqt_status gqt_set_vac_pair(gqt_ham* ham, int enable);
  * R > 1 rows, always use the FP64 pipe. */
 gqt_status gqt_set_fp64_arith(gqt_ham* ham, int mode);
 
-/* Temporal blocking of the paired-FP32 rows (Eq. 21 advanced two orders per
- * launch; default 1).  Applies to FP64 handles in paired-FP32 mode with R = 1
- * whose neighbour lists follow the honeycomb cell layout of the built-in
- * lattice (site 2(c1 + L1 c2) + s, A(c1,c2) bonded to B(c1,c2), B(c1+1,c2-1),
- * B(c1,c2-1), one slot order per sublattice, every row with three neighbours;
- * recognised when the handle is built, vacancies included), with L1 a multiple
- * of 32 cells and one segment.  Each CTA walks a band of 128 (or 64, 32) cells
- * down the rows: per row it computes T_{m+1} from T_m and T_{m-1}, and T_{m+2}
- * two rows behind from the T_{m+1} rows it wrote just before (still in L2), so
- * per two orders each orbital's vectors and hoppings come from DRAM once and
- * the index array is not read (VAC rows 160 bytes per orbital instead of 280,
- * l = r rows 96 instead of 184).  Each CTA recomputes the T_{m+1} values at its
- * band's edges itself.  Results agree with the single-order kernels to
- * rounding (the moment sums are split over CTAs differently).  The handle holds
- * two more vectors per chain.  0 = one order per launch; other handles always
- * run one order per launch. */
+/* Temporal blocking of the moment rows (Eq. 21 advanced two orders per
+ * launch; default 1).  Applies to handles whose neighbour lists follow the
+ * honeycomb cell layout of the built-in lattice (site 2(c1 + L1 c2) + s,
+ * A(c1,c2) bonded to B(c1,c2), B(c1+1,c2-1), B(c1,c2-1), one slot order per
+ * sublattice, every row with three neighbours; recognised when the handle is
+ * built, vacancies included) with one segment: FP64 handles in paired-FP32 mode
+ * with R = 1 and L1 a multiple of 32 cells, and FP32-storage handles with R = 2,
+ * 4, 8 or 16 vectors (one band per 128/(R/2), 64/(R/2) or 32/(R/2) cells, the
+ * largest dividing L1), run by the default multi-vector kernels.  Each CTA
+ * walks a band of cells (128, 64 or 32 for the FP64 handles) down the rows: per
+ * row it computes T_{m+1} from T_m and T_{m-1}, and T_{m+2} two rows behind from
+ * the T_{m+1} rows it wrote just before (still in L2), so per two orders each
+ * orbital's vectors and hoppings come from DRAM once and the index array is not
+ * read (FP64 VAC rows 160 bytes per orbital instead of 280, l = r rows 96
+ * instead of 184; FP32 VAC rows 64 + 16/R instead of 96 + 56/R).  Each CTA
+ * recomputes the T_{m+1} values at its band's edges itself.  Results agree with
+ * the single-order kernels to rounding (the chains are the same; the moment sums
+ * are split over CTAs differently).  The handle holds two more vectors per
+ * chain.  0 = one order per launch; other handles always run one order per
+ * launch. */
 gqt_status gqt_set_temporal_blocking(gqt_ham* ham, int enable);
 
 /* Blocked sweep order of the multi-vector kernels (default 1; built-in simple-
@@ -407,7 +411,8 @@ gqt_status gqt_set_graphs(gqt_ham* ham, int enable);
  * chain orders (gqt_kb_moments), 8 = Hall moment contraction (the M x M
  * complex GEMM), 9 = Kubo-Bastin energy sums (gqt_kubo_bastin), 10 =
  * temporally blocked passes of the two-recurrence rows (two steps, four moments
- * per launch), 11 = temporally blocked passes of the l = r rows.  Graph
+ * per launch), 11 = temporally blocked passes of the l = r rows, 12 and 13 =
+ * the same for FP32-storage handles with several vectors.  Graph
  * capture is bypassed while profiling. */
 gqt_status gqt_profile_start(void);
 gqt_status gqt_profile_stop(double* ms, uint64_t* launches, int ncat);

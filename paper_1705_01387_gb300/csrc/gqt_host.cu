@@ -840,7 +840,7 @@ static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const
                                                                  nzero);
         check_launch("k_cheb2_honey_df");
         if (fold) {
-          k_tl_fold<<<4, 128, 0, s2>>>(tscratch, tgrid, partial, nb, 2 * m - 2);
+          k_tl_fold<<<4, 128, 0, s2>>>(tscratch, tgrid, 1, partial, nb, 2 * m - 2);
           check_launch("k_tl_fold");
         }
         prof_end(pe, pair ? 10 : 11, s2);
@@ -936,6 +936,121 @@ static void launch_moments_df(gqt_ham* h, const void* l, const void* r, int M, v
   });
 }
 
+// Temporal blocking of the FP32 multi-vector rows (k_cheb2_honey_wv): FP32
+// handles whose rows follow the honeycomb cell layout, one segment, R = 2, 4, 8
+// or 16 vectors (G = R/2 lanes per site) and a band width dividing L1, when the
+// default multi-vector kernels run.  Returns log2 G, or -1 where it does not apply.
+static int tiled_wv_gs(const gqt_ham* h, int R) {
+  if (!h->use_tiling || h->prec != GQT_FP32_ACC64 || h->honey_L1 <= 0 || h->nseg != 1 || h->K != 3 ||
+      h->honey_L2 < 2 || !(h->variant == 2 || h->variant == 3) || h->threads > 128)
+    return -1;
+  const int gs = R == 2 ? 0 : R == 4 ? 1 : R == 8 ? 2 : R == 16 ? 3 : -1;
+  if (gs < 0 || tl_band_width_wv(h->honey_L1, 1 << gs) == 0) return -1;
+  return gs;
+}
+
+static size_t tl_wv_smem(int threads, int G) { return (size_t)8 * (threads / 32) * G * sizeof(double2); }
+
+template <bool CH, int NC>
+static int tiled_wv_grid(int threads, int G) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cheb2_honey_wv<CH, NC>, threads, tl_wv_smem(threads, G)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return std::max(1, n) * sm_count();
+}
+
+// Rows of an FP32 multi-vector handle with temporal blocking: the first order and
+// a last odd order by the single-order kernels, the orders between them two per
+// launch.  A chain's four buffers rotate: after step j, T_j is at cur and T_{j-1}
+// at prv (the caller's vector after step 1); a blocked pass writes T_{j+1} and
+// T_{j+2} into two buffers that hold neither, a single order writes T_{j+1} over
+// T_{j-1} when that is a buffer of the chain (same element, same thread).
+template <bool CH>
+static void wv_rows_tiled(gqt_ham* h, const Ell<false, CH>& H, const BlockTable& T, int R, int rs, bool pair,
+                          int steps, const float2* l, const float2* r, float2* const* A, float2* const* B, int gs,
+                          int tgrid, int tnseg, double2* partial, double2* tscratch, int slot_norm, cudaStream_t s2) {
+  const int nb = T.nblocks;
+  const Honey G = honey_of(h);
+  const int Gl = 1 << gs, bw = tl_band_width_wv(G.L1, Gl), thr = 2 * bw * Gl;
+  auto internal = [](float2* const* X, const float2* p) {
+    for (int b = 0; b < 4; ++b)
+      if (X[b] == p) return true;
+    return false;
+  };
+  auto free_of = [](float2* const* X, const float2* c, const float2* p, float2** f, int want) {
+    int n = 0;
+    for (int b = 0; b < 4 && n < want; ++b)
+      if (X[b] != c && X[b] != p) f[n++] = X[b];
+  };
+  size_t pe = prof_begin(s2);
+  if (pair)
+    launch_wave_pair<false, CH>(h, H, T, R, rs, l, r, (const float2*)nullptr, (const float2*)nullptr, A[0], B[0],
+                                partial, 1, slot_norm, s2);
+  else
+    launch_wave_dbl<false, CH>(h, H, T, R, rs, r, (const float2*)nullptr, B[0], partial, 1, s2);
+  check_launch(pair ? "k_cheb_pair_wv(first)" : "k_cheb_dbl_wv(first)");
+  prof_end(pe, 0, s2);
+  const float2 *ac = A[0], *ap = l, *bc = B[0], *bp = r;
+  for (int m = 2; m <= steps;) {
+    if (m + 1 <= steps) {
+      float2 *fa[2] = {nullptr, nullptr}, *fb[2] = {nullptr, nullptr};
+      free_of(B, bc, bp, fb, 2);
+      if (pair) free_of(A, ac, ap, fa, 2);
+      const bool fold = tgrid > nb;
+      double2* pout = fold ? tscratch : partial + (size_t)(2 * m - 2) * nb * R;
+      const int ostride = fold ? tgrid : nb, nzero = fold ? 0 : nb;
+      pe = prof_begin(s2);
+      if (pair)
+        k_cheb2_honey_wv<CH, 2><<<tgrid, thr, tl_wv_smem(thr, Gl), s2>>>(H, G, bw, tnseg, R, gs, ac, ap, bc, bp,
+                                                                        fa[0], fa[1], fb[0], fb[1], pout, ostride,
+                                                                        nzero);
+      else
+        k_cheb2_honey_wv<CH, 1><<<tgrid, thr, tl_wv_smem(thr, Gl), s2>>>(H, G, bw, tnseg, R, gs, bc, bp, nullptr,
+                                                                        nullptr, fb[0], fb[1], nullptr, nullptr,
+                                                                        pout, ostride, nzero);
+      check_launch("k_cheb2_honey_wv");
+      if (fold) {
+        k_tl_fold<<<4, 128, 0, s2>>>(tscratch, tgrid, R, partial, nb, 2 * m - 2);
+        check_launch("k_tl_fold");
+      }
+      prof_end(pe, pair ? 12 : 13, s2);
+      ap = fa[0];
+      ac = fa[1];
+      bp = fb[0];
+      bc = fb[1];
+      m += 2;
+    } else {
+      float2* bo = nullptr;
+      float2* ao = nullptr;
+      if (internal(B, bp))
+        bo = const_cast<float2*>(bp);
+      else
+        free_of(B, bc, bp, &bo, 1);
+      if (pair) {
+        if (internal(A, ap))
+          ao = const_cast<float2*>(ap);
+        else
+          free_of(A, ac, ap, &ao, 1);
+      }
+      pe = prof_begin(s2);
+      if (pair)
+        launch_wave_pair<false, CH>(h, H, T, R, rs, ac, bc, ap, bp, ao, bo, partial, m, slot_norm, s2);
+      else
+        launch_wave_dbl<false, CH>(h, H, T, R, rs, bc, bp, bo, partial, m, s2);
+      check_launch(pair ? "k_cheb_pair_wv" : "k_cheb_dbl_wv");
+      prof_end(pe, pair ? 6 : 5, s2);
+      ap = ac;
+      ac = ao;
+      bp = bc;
+      bc = bo;
+      m += 1;
+    }
+  }
+}
+
 // Launch the moment recursion of r against l and reduce into out, layout
 // [nseg][R][M].  kind 0: complex <l|T_m|r> (double2 out); kind 1: Re <l|T_m|r>
 // (double out); kind 2: l = r, Re <r|T_m|r> by the doubling identities
@@ -989,9 +1104,34 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
   const bool pair = kind == 1 && pair_applies(h, R);
   void* wa1 = pair ? h->ws(WS_PA1, vb).p : nullptr;
   void* wa2 = pair ? h->ws(WS_PA2, vb).p : nullptr;
-  const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p, wa1, wa2},
+  // temporally blocked FP32 rows: two more buffers per chain, the blocked grid
+  const int tgs = (pair || kind == 2) ? tiled_wv_gs(h, R) : -1;
+  void* tb[4] = {nullptr, nullptr, nullptr, nullptr};
+  int tgrid = 0, tnseg = 0;
+  double2* tscratch = nullptr;
+  if (tgs >= 0) {
+    tb[0] = h->ws(WS_TILE0, vb).p;
+    tb[1] = h->ws(WS_TILE0 + 1, vb).p;
+    if (pair) {
+      tb[2] = h->ws(WS_TILE0 + 2, vb).p;
+      tb[3] = h->ws(WS_TILE0 + 3, vb).p;
+    }
+    const int Gl = 1 << tgs, bw = tl_band_width_wv(h->honey_L1, Gl), thr = 2 * bw * Gl, nbands = h->honey_L1 / bw;
+    const int res = pair ? (h->hop_real ? tiled_wv_grid<false, 2>(thr, Gl) : tiled_wv_grid<true, 2>(thr, Gl))
+                         : (h->hop_real ? tiled_wv_grid<false, 1>(thr, Gl) : tiled_wv_grid<true, 1>(thr, Gl));
+    if (nbands <= res) {
+      tnseg = res / nbands;
+      tgrid = nbands * tnseg;
+    } else {
+      tgrid = res;
+    }
+    if (tgrid > nb)
+      tscratch = (double2*)h->ws(WS_TILE_SCRATCH, (size_t)4 * tgrid * R * sizeof(double2)).p;
+  }
+  const std::string key = key_of("mom", {l, r, out, w1, w2, partial, T.d_blk.p, wa1, wa2, tb[0], tb[1], tb[2], tb[3],
+                                         tscratch},
                                  {(double)kind, (double)R, (double)M, (double)h->threads, (double)nb,
-                                  (double)h->variant, (double)pair});
+                                  (double)h->variant, (double)pair, (double)tgs, (double)tgrid, (double)tnseg});
   run_graph(h, key, st, [&](cudaStream_t s2) {
     dispatch(h, [&](auto H) {
       using Tr = EllTraits<decltype(H)>;
@@ -1001,6 +1141,16 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
       V* W1 = (V*)w1;
       V* W2 = (V*)w2;
       const int* blk = (const int*)T.d_blk.p;
+      if constexpr (!Tr::fp64) {
+        if (tgs >= 0) {
+          float2* const A4[4] = {(float2*)wa1, (float2*)wa2, (float2*)tb[2], (float2*)tb[3]};
+          float2* const B4[4] = {(float2*)w1, (float2*)w2, (float2*)tb[0], (float2*)tb[1]};
+          const int steps = (M + 1) / 2;
+          wv_rows_tiled<Tr::ch>(h, H, T, R, rs, pair, std::max(steps, 1), (const float2*)l, (const float2*)r, A4, B4,
+                                tgs, tgrid, tnseg, partial, tscratch, 2 * steps, s2);
+          return;
+        }
+      }
       if (pair) {
         // chain A from l in wa1/wa2, chain B from r in W1/W2; step m yields the dots of
         // moments 2m-2 and 2m-1, and step 1 the norms (slot 2 * steps)

@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
     }
     __syncthreads();
     const TlCols C(G, B1 + cc, s);
-    for (int t = 0; t <= S + 2; ++t) {
+    // the rows that the first order streams, two rows ahead, into L2 (two chains)
+    auto prefetch = [&](int t) {
       if (NC == 2 && threadIdx.x < 8) {
-        // the rows that the first order streams, two rows ahead, into L2
         const int yp = y0 + 1 + t;
         if (yp <= y0 + S) {
           const int i0 = 2 * (B1 + G.L1 * (yp - (yp >= G.L2 ? G.L2 : 0)));
@@ -208,29 +208,78 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
           if (lane == 7) tl_prefetch_l2(H.diag + i0, (uint32_t)nsite * 8u);
         }
       }
-      if (t <= S + 1) {  // T_{m+1} on row y0 - 1 + t (rows y0 - 1 and y0 + S only as halo)
-        int j[3];
-        const int i = C.at(G, y0 - 1 + t, j);
-        TlSite<CH, NC> T;
-        tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
-        float4 v[NC];
-        tl_compute<CH, NC>(T, v);
-        za[i] = v[0];
-        if (NC == 2) zb[i] = v[NC - 1];
-        if (t >= 1 && t <= S) tl_dots<NC>(q0, q1, T.own, v);
+    };
+    // T_{m+1} on row y0 - 1 + t (rows y0 - 1 and y0 + S only as halo)
+    auto first = [&](int t) {
+      int j[3];
+      const int i = C.at(G, y0 - 1 + t, j);
+      TlSite<CH, NC> T;
+      tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
+      float4 v[NC];
+      tl_compute<CH, NC>(T, v);
+      za[i] = v[0];
+      if (NC == 2) zb[i] = v[NC - 1];
+      if (t >= 1 && t <= S) tl_dots<NC>(q0, q1, T.own, v);
+    };
+    // T_{m+2} on row y0 + t - 3: its T_{m+1} rows were written in earlier iterations
+    auto second = [&](int t) {
+      int j[3];
+      const int i = C.at(G, y0 + t - 3, j);
+      TlSite<CH, NC> U;
+      tl_load<CH, NC, false>(U, H, i, j, za, zb, xa, xb);
+      float4 v[NC];
+      tl_compute<CH, NC>(U, v);
+      wa[i] = v[0];
+      if (NC == 2) wb[i] = v[NC - 1];
+      tl_dots<NC>(q2, q3, U.own, v);
+    };
+    // With one chain the second order comes first in the iterations that do
+    // both, so that the first order's loads (inputs of the launch, never written
+    // by it) need not wait for the second order's stores (l = r pass 375 -> 349
+    // us at N = 16.8M); the two-chain pass keeps one loop in which the first
+    // order comes first.
+    if constexpr (NC == 1) {
+      int t = 0;
+      for (; t <= min(2, S + 1); ++t) {
+        first(t);
+        __syncthreads();
       }
-      if (t >= 3) {  // T_{m+2} on row y0 + t - 3: its T_{m+1} rows were written in earlier iterations
-        int j[3];
-        const int i = C.at(G, y0 + t - 3, j);
-        TlSite<CH, NC> U;
-        tl_load<CH, NC, false>(U, H, i, j, za, zb, xa, xb);
-        float4 v[NC];
-        tl_compute<CH, NC>(U, v);
-        wa[i] = v[0];
-        if (NC == 2) wb[i] = v[NC - 1];
-        tl_dots<NC>(q2, q3, U.own, v);
+      for (; t <= S + 1; ++t) {
+        second(t);
+        first(t);
+        __syncthreads();
       }
-      __syncthreads();
+      for (; t <= S + 2; ++t) {
+        second(t);
+        __syncthreads();
+      }
+    } else {
+      for (int t = 0; t <= S + 2; ++t) {
+        prefetch(t);
+        if (t <= S + 1) {
+          int j[3];
+          const int i = C.at(G, y0 - 1 + t, j);
+          TlSite<CH, NC> T;
+          tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
+          float4 v[NC];
+          tl_compute<CH, NC>(T, v);
+          za[i] = v[0];
+          if (NC == 2) zb[i] = v[NC - 1];
+          if (t >= 1 && t <= S) tl_dots<NC>(q0, q1, T.own, v);
+        }
+        if (t >= 3) {
+          int j[3];
+          const int i = C.at(G, y0 + t - 3, j);
+          TlSite<CH, NC> U;
+          tl_load<CH, NC, false>(U, H, i, j, za, zb, xa, xb);
+          float4 v[NC];
+          tl_compute<CH, NC>(U, v);
+          wa[i] = v[0];
+          if (NC == 2) wb[i] = v[NC - 1];
+          tl_dots<NC>(q2, q3, U.own, v);
+        }
+        __syncthreads();
+      }
     }
   }
   double r[4] = {q0.get(), q1.get(), q2.get(), q3.get()};
@@ -245,18 +294,240 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
     if (threadIdx.x < 4) pout[(size_t)threadIdx.x * ostride + b] = make_double2(0.0, 0.0);
 }
 
-// Sum of the blocked kernel's per-CTA partials (4 slots of ngrid entries, CTA
-// order) into entry 0 of the moment slots slot0 .. slot0 + 3 (stride nblocks),
+// ---------------------------------------------------------------- FP32 storage, R vectors
+
+// Band width (cells) of the FP32 multi-vector walk for G lanes per site: the
+// largest of 128/G, 64/G, 32/G dividing L1 (0: none), so that a CTA has at
+// most 256 threads (two sites per cell, G lanes per site).
+__host__ __device__ inline int tl_band_width_wv(int L1, int G) {
+  for (int c = 128; c >= 32; c >>= 1) {
+    const int bw = c / G;
+    if (bw >= 1 && L1 % bw == 0) return bw;
+  }
+  return 0;
+}
+
+// One chain value of VP = 2 vectors at a site: a 16-byte load of the lane's two
+// complex64 elements (vectors 2g and 2g + 1 of the site's row of R).
+template <int MODE>  // 0: read-only path, 1: coherent (vectors this launch writes), 2: evict-first stream
+__device__ __forceinline__ void tl_ld2(float2 (&d)[2], const float2* p, size_t e) {
+  float4 t;
+  if (MODE == 0)
+    t = __ldg(reinterpret_cast<const float4*>(p + e));
+  else if (MODE == 1)
+    t = *reinterpret_cast<const float4*>(p + e);
+  else
+    t = __ldcs(reinterpret_cast<const float4*>(p + e));
+  d[0] = make_float2(t.x, t.y);
+  d[1] = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void tl_st2(float2* p, size_t e, const float2 (&d)[2]) {
+  *reinterpret_cast<float4*>(p + e) = make_float4(d[0].x, d[0].y, d[1].x, d[1].y);
+}
+
+// The operands of one order at a site for the lane's two vectors, NC chains.
+template <bool CH, int NC>
+struct TlSiteWv {
+  typename Ell<false, CH>::HT hv[3];
+  float dg;
+  float2 own[NC][2], nb[NC][3][2], prev[NC][2];
+};
+
+template <bool CH, int NC, bool IN_RO>
+__device__ __forceinline__ void tl_load_wv(TlSiteWv<CH, NC>& S, const Ell<false, CH>& H, int i, const int (&j)[3],
+                                           int R, int off, const float2* in0, const float2* in1,
+                                           const float2* __restrict__ pv0, const float2* __restrict__ pv1) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) S.hv[k] = __ldg(H.hop2 + (size_t)k * H.n + i);
+  S.dg = __ldg(H.diag2 + i);
+  const size_t e = (size_t)i * R + off;
+#pragma unroll
+  for (int ch = 0; ch < NC; ++ch) {
+    const float2* in = ch ? in1 : in0;
+    tl_ld2<IN_RO ? 0 : 1>(S.own[ch], in, e);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tl_ld2<IN_RO ? 0 : 1>(S.nb[ch][k], in, (size_t)j[k] * R + off);
+    tl_ld2<2>(S.prev[ch], ch ? pv1 : pv0, e);
+  }
+}
+
+// T = 2H~ T_in - T_prev for the lane's two vectors of each chain, in FP32, with
+// the fused multiply-adds in the order of the single-order kernels (two chains:
+// diagonal first, as k_cheb_pair_wv; one chain: neighbours first, as
+// k_cheb_dbl_wv), so that the chains equal theirs bit for bit.
+template <bool CH, int NC>
+__device__ __forceinline__ void tl_compute_wv(const TlSiteWv<CH, NC>& S, float2 (&v)[NC][2]) {
+#pragma unroll
+  for (int ch = 0; ch < NC; ++ch)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float2 a = cneg(S.prev[ch][q]);
+      if (NC == 2) a = cmul_acc(a, S.dg, S.own[ch][q]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a = cmul_acc(a, S.hv[k], S.nb[ch][k][q]);
+      if (NC == 1) a = cmul_acc(a, S.dg, S.own[ch][q]);
+      v[ch][q] = a;
+    }
+}
+
+// Dots of one order: NC = 2, Re <A_k|B_k> and Re <A_k|B_k+1>; NC = 1, <u_k|u_k>
+// and Re <u_k+1|u_k> (per vector, FP32 compensated sums).
+template <int NC>
+__device__ __forceinline__ void tl_dots_wv(DotAcc<float2> (&p)[2], DotAcc<float2> (&q)[2],
+                                           const float2 (&own)[NC][2], const float2 (&v)[NC][2]) {
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    if (NC == 2) {
+      p[w].add_re(own[0][w], own[NC - 1][w]);
+      q[w].add_re(own[0][w], v[NC - 1][w]);
+    } else {
+      p[w].add_norm(own[0][w]);
+      q[w].add_re(v[0][w], own[0][w]);
+    }
+  }
+}
+
+// Two orders per launch for FP32-storage handles with R = 2G vectors per site
+// (G = 1, 2, 4, 8 lanes per site, lane g holding vectors 2g and 2g + 1, the
+// vector rows of the multi-vector kernels): the band walk of k_cheb2_honey_df
+// with a band of bw cells served by 2 bw G <= 256 threads, FP32 arithmetic (the
+// recursion of the FP32 kernels) and FP32 compensated dots per vector,
+// converted to FP64 once per thread and reduced per vector into the partial
+// slots [slot][CTA][R] of the multi-vector kernels.  Per two orders and
+// orbital, DRAM moves T_m, T_{m-1} and the two outputs once, 8 bytes each per
+// chain, plus H~ once per site and no index array: for the two-recurrence rows
+// 64 + 16/R bytes instead of 2 x (48 + 28/R) for two single-order launches.
+template <bool CH, int NC>
+__global__ void __launch_bounds__(256, 3) k_cheb2_honey_wv(
+    Ell<false, CH> H, Honey G, int bw, int nseg, int R, int gs, const float2* __restrict__ xa,
+    const float2* __restrict__ ya, const float2* __restrict__ xb, const float2* __restrict__ yb, float2* za,
+    float2* __restrict__ wa, float2* zb, float2* __restrict__ wb, double2* __restrict__ pout, int ostride,
+    int nzero) {
+  const int Gl = 1 << gs;
+  const int lg = (int)threadIdx.x & (Gl - 1);
+  const int st = (int)threadIdx.x >> gs;  // site of the band row: cell B1 + st / 2, sublattice st % 2
+  const int s = st & 1, cc = st >> 1;
+  const int off = 2 * lg;
+  const int nbands = G.L1 / bw;
+  long long r_beg, r_end;  // band rows, band-major
+  if (nseg > 0) {
+    const int band = (int)blockIdx.x % nbands, seg = (int)blockIdx.x / nbands;
+    r_beg = (long long)band * G.L2 + (long long)G.L2 * seg / nseg;
+    r_end = (long long)band * G.L2 + (long long)G.L2 * (seg + 1) / nseg;
+  } else {
+    const long long total = (long long)nbands * G.L2;
+    r_beg = total * blockIdx.x / gridDim.x;
+    r_end = total * (blockIdx.x + 1) / gridDim.x;
+  }
+  DotAcc<float2> q0[2], q1[2], q2[2], q3[2];
+  for (long long p = r_beg; p < r_end;) {
+    const int band = (int)(p / G.L2), y0 = (int)(p % G.L2);
+    const int S = (int)min((long long)(G.L2 - y0), r_end - p);
+    p += S;
+    const int B1 = band * bw;
+    // T_{m+1} on the halo columns (A at cell B1 - 1, B at cell B1 + bw) of rows y0 - 1 .. y0 + S
+    for (int q = threadIdx.x; q < 2 * (S + 2) * Gl; q += blockDim.x) {
+      const int hl = q & (Gl - 1), hq = q >> gs;
+      const int hs = hq & 1, c1 = hs ? B1 + bw : B1 - 1;
+      const TlCols C(G, c1 + (c1 < 0 ? G.L1 : 0) - (c1 >= G.L1 ? G.L1 : 0), hs);
+      int j[3];
+      const int i = C.at(G, y0 - 1 + (hq >> 1), j);
+      TlSiteWv<CH, NC> T;
+      tl_load_wv<CH, NC, true>(T, H, i, j, R, 2 * hl, xa, xb, ya, yb);
+      float2 v[NC][2];
+      tl_compute_wv<CH, NC>(T, v);
+      const size_t e = (size_t)i * R + 2 * hl;
+      tl_st2(za, e, v[0]);
+      if (NC == 2) tl_st2(zb, e, v[NC - 1]);
+    }
+    __syncthreads();
+    const TlCols C(G, B1 + cc, s);
+    // iteration t: T_{m+1} on row y0 - 1 + t (t <= S + 1; rows y0 - 1 and y0 + S
+    // only as halo) and T_{m+2} on row y0 + t - 3 (t >= 3; its T_{m+1} rows were
+    // written in earlier iterations).  With one chain the second order comes
+    // first, so that in the steady iterations the first order's loads (inputs of
+    // the launch, never written by it) need not wait for the second order's
+    // stores (measured: l = r pass 590 -> 547 us at the precision workload); the
+    // two-chain pass, whose operands take twice the registers, keeps one loop in
+    // which the first order comes first (the other order measured 928 -> 992 us).
+    auto first = [&](int t) {
+      int j[3];
+      const int i = C.at(G, y0 - 1 + t, j);
+      TlSiteWv<CH, NC> T;
+      tl_load_wv<CH, NC, true>(T, H, i, j, R, off, xa, xb, ya, yb);
+      float2 v[NC][2];
+      tl_compute_wv<CH, NC>(T, v);
+      const size_t e = (size_t)i * R + off;
+      tl_st2(za, e, v[0]);
+      if (NC == 2) tl_st2(zb, e, v[NC - 1]);
+      if (t >= 1 && t <= S) tl_dots_wv<NC>(q0, q1, T.own, v);
+    };
+    auto second = [&](int t) {
+      int j[3];
+      const int i = C.at(G, y0 + t - 3, j);
+      TlSiteWv<CH, NC> U;
+      tl_load_wv<CH, NC, false>(U, H, i, j, R, off, za, zb, xa, xb);
+      float2 v[NC][2];
+      tl_compute_wv<CH, NC>(U, v);
+      const size_t e = (size_t)i * R + off;
+      __stcs(reinterpret_cast<float4*>(wa + e), make_float4(v[0][0].x, v[0][0].y, v[0][1].x, v[0][1].y));
+      if (NC == 2)
+        __stcs(reinterpret_cast<float4*>(wb + e),
+               make_float4(v[NC - 1][0].x, v[NC - 1][0].y, v[NC - 1][1].x, v[NC - 1][1].y));
+      tl_dots_wv<NC>(q2, q3, U.own, v);
+    };
+    if constexpr (NC == 1) {
+      int t = 0;
+      for (; t <= min(2, S + 1); ++t) {
+        first(t);
+        __syncthreads();
+      }
+      for (; t <= S + 1; ++t) {
+        second(t);
+        first(t);
+        __syncthreads();
+      }
+      for (; t <= S + 2; ++t) {
+        second(t);
+        __syncthreads();
+      }
+    } else {
+      for (int t = 0; t <= S + 2; ++t) {
+        if (t <= S + 1) first(t);
+        if (t >= 3) second(t);
+        __syncthreads();
+      }
+    }
+  }
+  double2 r[8];
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    r[w] = q0[w].get();
+    r[2 + w] = q1[w].get();
+    r[4 + w] = q2[w].get();
+    r[6 + w] = q3[w].get();
+  }
+  const int slots[4] = {0, 1, 2, 3};
+  write_partials_vpt<false, 2, 4>(r, R, Gl, dyn_smem(), pout, ostride, slots);
+  // entries gridDim.x .. nzero - 1 of each slot hold zero
+  for (int b = blockIdx.x + gridDim.x; b < nzero; b += gridDim.x)
+    for (int t = threadIdx.x; t < 4 * R; t += blockDim.x)
+      pout[((size_t)(t / R) * ostride + b) * R + t % R] = make_double2(0.0, 0.0);
+}
+
+// Sum of the blocked kernel's per-CTA partials (4 slots of ngrid x R entries, CTA
+// order) into entry 0 of the moment slots slot0 .. slot0 + 3 (stride nblocks x R),
 // the other entries zero: used when the blocked grid is larger than the
 // single-order grid whose size the slots have.
-__global__ void k_tl_fold(const double2* __restrict__ scratch, int ngrid, double2* __restrict__ partial, int nblocks,
-                          int slot0) {
+__global__ void k_tl_fold(const double2* __restrict__ scratch, int ngrid, int R, double2* __restrict__ partial,
+                          int nblocks, int slot0) {
   const int j = (int)blockIdx.x;  // slot
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+  for (int t = threadIdx.x; t < nblocks * R; t += blockDim.x) {
+    const int b = t / R, r = t % R;
     double v = 0.0;
     if (b == 0)
-      for (int c = 0; c < ngrid; ++c) v += scratch[(size_t)j * ngrid + c].x;
-    partial[(size_t)(slot0 + j) * nblocks + b] = make_double2(v, 0.0);
+      for (int c = 0; c < ngrid; ++c) v += scratch[((size_t)j * ngrid + c) * R + r].x;
+    partial[((size_t)(slot0 + j) * nblocks + b) * R + r] = make_double2(v, 0.0);
   }
 }
 
