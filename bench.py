@@ -254,8 +254,8 @@ def precision_table(args, g, torch):
     normalised L-infinity over n (moments) or E, per vector, maximised over the
     reference vectors and rows; the VAC row error is also reported per step."""
     w = S.config(3, small=args.small)
-    L1 = w.lattice_args["L1"]
-    M, R, Nt = w.M, w.R, args.precision_steps
+    L1 = args.precision_L or w.lattice_args["L1"]
+    M, R, Nt = args.precision_moments or w.M, w.R, args.precision_steps
     nref = max(1, min(args.precision_ref_vectors, R))
     Nm = max(1, min(args.precision_msd_steps, Nt))
     dE = w.energy_scale
@@ -850,6 +850,8 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=200, help="VAC time steps of the error table")
     ap.add_argument("--precision-msd-steps", type=int, default=3, help="MSD time steps of the error table")
     ap.add_argument("--precision-ref-vectors", type=int, default=2, help="FP64 reference vectors of the error table")
+    ap.add_argument("--precision-L", type=int, default=0, help="honeycomb cells per side of the error table (profiling)")
+    ap.add_argument("--precision-moments", type=int, default=0, help="moments of the error table (profiling)")
     ap.add_argument("--hall", action="store_true", help="Hall conductivity (Kubo-Bastin) of the Haldane model")
     ap.add_argument("--hall-L", type=int, default=0, help="Haldane cells per side of the Hall run (profiling)")
     ap.add_argument("--hall-moments", type=int, default=0, help="Kubo-Bastin moments of the Hall run (profiling)")

@@ -191,24 +191,6 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
     }
     __syncthreads();
     const TlCols C(G, B1 + cc, s);
-    // the rows that the first order streams, two rows ahead, into L2 (two chains)
-    auto prefetch = [&](int t) {
-      if (NC == 2 && threadIdx.x < 8) {
-        const int yp = y0 + 1 + t;
-        if (yp <= y0 + S) {
-          const int i0 = 2 * (B1 + G.L1 * (yp - (yp >= G.L2 ? G.L2 : 0)));
-          const int lane = threadIdx.x;
-          const uint32_t vb = (uint32_t)nsite * 16u;
-          if (lane == 0) tl_prefetch_l2(xa + i0, vb);
-          if (lane == 1) tl_prefetch_l2(ya + i0, vb);
-          if (lane == 2) tl_prefetch_l2(xb + i0, vb);
-          if (lane == 3) tl_prefetch_l2(yb + i0, vb);
-          if (lane >= 4 && lane < 7)
-            tl_prefetch_l2(H.hop + (size_t)(lane - 4) * H.n + i0, (uint32_t)(nsite * sizeof(typename DfHop<CH>::T)));
-          if (lane == 7) tl_prefetch_l2(H.diag + i0, (uint32_t)nsite * 8u);
-        }
-      }
-    };
     // T_{m+1} on row y0 - 1 + t (rows y0 - 1 and y0 + S only as halo)
     auto first = [&](int t) {
       int j[3];
@@ -255,7 +237,23 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
       }
     } else {
       for (int t = 0; t <= S + 2; ++t) {
-        prefetch(t);
+        if (threadIdx.x < 8) {
+          // the rows that the first order streams, two rows ahead, into L2
+          const int yp = y0 + 1 + t;
+          if (yp <= y0 + S) {
+            const int i0 = 2 * (B1 + G.L1 * (yp - (yp >= G.L2 ? G.L2 : 0)));
+            const int lane = threadIdx.x;
+            const uint32_t vb = (uint32_t)nsite * 16u;
+            if (lane == 0) tl_prefetch_l2(xa + i0, vb);
+            if (lane == 1) tl_prefetch_l2(ya + i0, vb);
+            if (lane == 2) tl_prefetch_l2(xb + i0, vb);
+            if (lane == 3) tl_prefetch_l2(yb + i0, vb);
+            if (lane >= 4 && lane < 7)
+              tl_prefetch_l2(H.hop + (size_t)(lane - 4) * H.n + i0,
+                             (uint32_t)(nsite * sizeof(typename DfHop<CH>::T)));
+            if (lane == 7) tl_prefetch_l2(H.diag + i0, (uint32_t)nsite * 8u);
+          }
+        }
         if (t <= S + 1) {
           int j[3];
           const int i = C.at(G, y0 - 1 + t, j);
