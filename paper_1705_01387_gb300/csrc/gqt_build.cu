@@ -549,6 +549,7 @@ extern "C" gqt_status gqt_update_hamiltonian(gqt_ham* h, const double* onsite, c
       put(h->d_hop, hop.data(), hop.size() * 8);
       put(h->d_diag, dg.data(), dg.size() * 8);
       h->df_ready = false;  // the (hi, lo) split of 2H~ is taken again on next use
+      h->dfx_ready = false;
     } else {
       std::vector<float> hop(n * K * hw), dg(n);
       for (int64_t i = 0; i < n; ++i) {

@@ -47,6 +47,7 @@ struct DfEll {
   const int* idx = nullptr;                    // [K][n]
   const typename DfHop<CH>::T* hop = nullptr;  // [K][n]
   const float2* diag = nullptr;                // [n]
+  const typename DfHop<CH>::T* xhop = nullptr;  // [K][n] 2[X,H~]_ij = -dx_ij 2H~_ij (commutator orders)
 };
 
 // ---------------------------------------------------------------- pair arithmetic
@@ -144,6 +145,23 @@ __global__ void k_split_hamiltonian(long long nslots, const void* __restrict__ h
   }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
     diag_df[i] = df_split(diag64[i]);
+}
+
+// 2[X,H~] slot values -dx_ij 2H~_ij (Eq. 34 with [X,H]_ij = -dx_ij H_ij) as pairs,
+// formed in FP64 and split once per handle.
+template <bool CH>
+__global__ void k_split_xhop(long long nslots, const void* __restrict__ hop64, const double* __restrict__ dx,
+                             void* __restrict__ xhop_df) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslots; s += stride) {
+    const double d = -dx[s];
+    if (CH) {
+      const double2 h = ((const double2*)hop64)[s];
+      ((float4*)xhop_df)[s] = df_split(make_double2(d * h.x, d * h.y));
+    } else {
+      ((float2*)xhop_df)[s] = df_split(d * ((const double*)hop64)[s]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- moment rows
@@ -305,6 +323,231 @@ __global__ void __launch_bounds__(256, 3) k_cheb_dbl_df(DfEll<CH> H, const int4*
     const int k0 = 2 * m - 2;
     partial[(size_t)k0 * nblocks + b] = make_double2(v[0], 0.0);
     partial[(size_t)(k0 + 1) * nblocks + b] = make_double2(v[1], 0.0);
+  }
+}
+
+// ---------------------------------------------------------------- evolution
+
+// U(dt) psi = sum_m c_m T_m(H~) psi (Eq. 17) for NSET vector sets sharing H~,
+// R = 1, on pairs of FP32 numbers: the chains T_m as pairs (16 bytes per complex
+// element, the size of the FP64 workspace), the sum of c_m T_m as pairs, the
+// caller's FP64 vectors split at the first order and formed again at the last
+// (hi + lo of two FP32 numbers is exact in FP64).  Orders by phase:
+//   PH 0 (m = 0, 1): out = T_1 = H~ psi, t0 = psi as pairs, acc = c0 psi + c1 T_1;
+//                    |psi|^2 partials (slot);
+//   PH 1 (2 <= m < Np - 1): out = 2H~ t1 - t2 (over t2, same element and thread),
+//                    acc += c0 out;
+//   PH 2 (m = Np - 1): psi = acc + c0 (2H~ t1 - t2) in FP64, |psi|^2 partials;
+//   PH 3 (Np <= 2): psi = acc in FP64, |psi|^2 partials.
+// c0, c1: complex coefficients as pairs (re.hi, re.lo, im.hi, im.lo).  The
+// partial slots are those of k_evolve (k_norm_check reads them).
+template <int NSET>
+struct DfEvo {
+  double2* psi[NSET];
+  const float4* t1[NSET];
+  const float4* t2[NSET];
+  float4* out[NSET];
+  float4* t0[NSET];
+  float4* acc[NSET];
+};
+
+__device__ __forceinline__ double2 df_to_d2(float4 f) { return make_double2(df_value(f.x, f.y), df_value(f.z, f.w)); }
+__device__ __forceinline__ DfC dfc_of(float4 a) { return DfC{a.x, a.y, a.z, a.w}; }
+
+template <bool CH, int KK>
+__device__ __forceinline__ void df_row_ops(const DfEll<CH>& H, int i, int (&idx)[KK],
+                                           typename DfHop<CH>::T (&hv)[KK], float2& dg) {
+#pragma unroll
+  for (int k = 0; k < KK; ++k) {
+    const size_t s = (size_t)k * H.n + i;
+    idx[k] = __ldg(H.idx + s);
+    hv[k] = __ldg(H.hop + s);
+  }
+  dg = __ldg(H.diag + i);
+}
+
+template <bool CH, int KK, int NSET, int PH>
+__global__ void __launch_bounds__(256) k_evolve_df(DfEll<CH> H, const int4* __restrict__ tab, DfEvo<NSET> A,
+                                                   float4 c0, float4 c1, double2* __restrict__ partial, int nblocks,
+                                                   int slot) {
+  using HT = typename DfHop<CH>::T;
+  const int4 tb = tab[blockIdx.x];
+  const size_t sege = (size_t)tb.y, step = (size_t)tb.w * blockDim.x;
+  DfDot nrm[NSET];
+  for (size_t e = (size_t)tb.x + (size_t)tb.z * blockDim.x + threadIdx.x; e < sege; e += step) {
+    const int i = (int)e;
+    if (PH == 3) {
+#pragma unroll
+      for (int q = 0; q < NSET; ++q) {
+        const float4 f = A.acc[q][e];
+        A.psi[q][e] = df_to_d2(f);
+        nrm[q].add_norm(f);
+      }
+      continue;
+    }
+    int idx[KK];
+    HT hv[KK];
+    float2 dg;
+    df_row_ops<CH, KK>(H, i, idx, hv, dg);
+#pragma unroll
+    for (int q = 0; q < NSET; ++q) {
+      float4 nb[KK];
+      if (PH == 0) {
+        const float4 own = df_load<true>(A.psi[q], e);
+#pragma unroll
+        for (int k = 0; k < KK; ++k) nb[k] = df_load<true>(A.psi[q], (size_t)idx[k]);
+        const float4 y = df_step<CH, KK, true>(hv, dg, own, nb, make_float4(0.f, 0.f, 0.f, 0.f));
+        A.out[q][e] = y;
+        A.t0[q][e] = own;
+        DfC a = dfc_zero();
+        dfc_mac(a, c0, own);
+        dfc_mac(a, c1, y);
+        A.acc[q][e] = dfc_out(a, false);
+        nrm[q].add_norm(own);
+      } else {
+        const float4 own = __ldg(A.t1[q] + e);
+#pragma unroll
+        for (int k = 0; k < KK; ++k) nb[k] = __ldg(A.t1[q] + idx[k]);
+        const float4 y = df_step<CH, KK, false>(hv, dg, own, nb, A.t2[q][e]);
+        DfC a = dfc_of(A.acc[q][e]);
+        dfc_mac(a, c0, y);
+        const float4 f = dfc_out(a, false);
+        if (PH == 1) {
+          A.out[q][e] = y;
+          A.acc[q][e] = f;
+        } else {
+          A.psi[q][e] = df_to_d2(f);
+          nrm[q].add_norm(f);
+        }
+      }
+    }
+  }
+  if (PH != 1) {
+    double v[NSET];
+#pragma unroll
+    for (int q = 0; q < NSET; ++q) v[q] = nrm[q].get();
+    block_reduce_rx<NSET>(v, 1, reinterpret_cast<double*>(dyn_smem()));
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NSET; ++q) partial[(size_t)(slot + q) * nblocks + blockIdx.x] = make_double2(v[q], 0.0);
+    }
+  }
+}
+
+// One MSD time step's coupled orders (Eqs. 17, 18, 22, 24) on pairs, R = 1:
+//   u_m = T_m(H~) p,  z_m = [X, T_m] p + T_m px,
+//   z_m = 2[X,H~] u_{m-1} + 2H~ z_{m-1} - z_{m-2}  (z_1 = [X,H~] p + H~ px),
+//   accp += c_m u_m (-> U(dt) p), accx += c_m z_m (-> [X,U(dt)]p + U(dt)px).
+// Phases as k_evolve_df (PH 0 also writes p and px as pairs into u0, z0); the
+// partial slots are those of k_msd_evolve (k_norm_check_msd reads them).
+struct DfMsd {
+  double2* p;
+  double2* px;
+  const float4* u1;
+  const float4* u2;
+  const float4* z1;
+  const float4* z2;
+  float4* uo;
+  float4* zo;
+  float4* u0;
+  float4* z0;
+  float4* accp;
+  float4* accx;
+};
+
+template <bool CH, int KK, int PH>
+__global__ void __launch_bounds__(256) k_msd_evolve_df(DfEll<CH> H, const int4* __restrict__ tab, DfMsd B, float4 c0,
+                                                       float4 c1, double2* __restrict__ partial, int nblocks,
+                                                       int slot) {
+  using HT = typename DfHop<CH>::T;
+  const int4 tb = tab[blockIdx.x];
+  const size_t sege = (size_t)tb.y, step = (size_t)tb.w * blockDim.x;
+  DfDot n0, n1;
+  for (size_t e = (size_t)tb.x + (size_t)tb.z * blockDim.x + threadIdx.x; e < sege; e += step) {
+    const int i = (int)e;
+    if (PH == 3) {
+      const float4 fp = B.accp[e], fx = B.accx[e];
+      B.p[e] = df_to_d2(fp);
+      B.px[e] = df_to_d2(fx);
+      n0.add_norm(fp);
+      n1.add_norm(fx);
+      continue;
+    }
+    int idx[KK];
+    HT hv[KK];
+    float2 dg;
+    df_row_ops<CH, KK>(H, i, idx, hv, dg);
+    float4 uo, zo;  // u_m and z_m at this element
+    float4 u_own, z_own;
+    if (PH == 0) {
+      u_own = df_load<true>(B.p, e);
+      z_own = df_load<true>(B.px, e);
+      float4 un[KK];
+#pragma unroll
+      for (int k = 0; k < KK; ++k) un[k] = df_load<true>(B.p, (size_t)idx[k]);
+      uo = df_step<CH, KK, true>(hv, dg, u_own, un, make_float4(0.f, 0.f, 0.f, 0.f));
+      DfC a = dfc_zero();
+      dfc_mac(a, dg, z_own);
+#pragma unroll
+      for (int k = 0; k < KK; ++k) {
+        dfc_mac(a, hv[k], df_load<true>(B.px, (size_t)idx[k]));
+        dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
+      }
+      zo = dfc_out(a, true);
+    } else {
+      u_own = __ldg(B.u1 + e);
+      z_own = __ldg(B.z1 + e);
+      float4 un[KK];
+#pragma unroll
+      for (int k = 0; k < KK; ++k) un[k] = __ldg(B.u1 + idx[k]);
+      uo = df_step<CH, KK, false>(hv, dg, u_own, un, B.u2[e]);
+      DfC a = dfc_neg(B.z2[e]);
+      dfc_mac(a, dg, z_own);
+#pragma unroll
+      for (int k = 0; k < KK; ++k) {
+        dfc_mac(a, hv[k], __ldg(B.z1 + idx[k]));
+        dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
+      }
+      zo = dfc_out(a, false);
+    }
+    if (PH == 0) {
+      B.uo[e] = uo;
+      B.zo[e] = zo;
+      B.u0[e] = u_own;
+      B.z0[e] = z_own;
+      DfC ap = dfc_zero(), ax = dfc_zero();
+      dfc_mac(ap, c0, u_own);
+      dfc_mac(ap, c1, uo);
+      dfc_mac(ax, c0, z_own);
+      dfc_mac(ax, c1, zo);
+      B.accp[e] = dfc_out(ap, false);
+      B.accx[e] = dfc_out(ax, false);
+      n0.add_norm(u_own);
+    } else {
+      DfC ap = dfc_of(B.accp[e]), ax = dfc_of(B.accx[e]);
+      dfc_mac(ap, c0, uo);
+      dfc_mac(ax, c0, zo);
+      const float4 fp = dfc_out(ap, false), fx = dfc_out(ax, false);
+      if (PH == 1) {
+        B.uo[e] = uo;
+        B.zo[e] = zo;
+        B.accp[e] = fp;
+        B.accx[e] = fx;
+      } else {
+        B.p[e] = df_to_d2(fp);
+        B.px[e] = df_to_d2(fx);
+        n0.add_norm(fp);
+        n1.add_norm(fx);
+      }
+    }
+  }
+  if (PH != 1) {
+    double v[2] = {n0.get(), n1.get()};
+    block_reduce_rx<2>(v, 1, reinterpret_cast<double*>(dyn_smem()));
+    if (threadIdx.x == 0) {
+      partial[(size_t)slot * nblocks + blockIdx.x] = make_double2(v[0], 0.0);
+      partial[(size_t)(slot + 1) * nblocks + blockIdx.x] = make_double2(v[1], 0.0);
+    }
   }
 }
 

@@ -723,7 +723,25 @@ static DfEll<CH> df_ell_of(const gqt_ham* h) {
   e.idx = (const int*)h->d_idx.p;
   e.hop = (const typename DfHop<CH>::T*)h->d_hop_df.p;
   e.diag = (const float2*)h->d_diag_df.p;
+  e.xhop = (const typename DfHop<CH>::T*)h->d_xhop_df.p;
   return e;
+}
+
+// 2[X,H~] slot values as pairs for the commutator orders (once per handle, again
+// after gqt_update_hamiltonian).  Runs on the call's stream before any capture.
+static void ensure_df_x(gqt_ham* h, cudaStream_t st) {
+  if (h->dfx_ready) return;
+  const size_t nslots = (size_t)h->K * h->n;
+  h->d_xhop_df.ensure(nslots * (h->hop_real ? sizeof(float2) : sizeof(float4)));
+  const int blocks = sm_count() * 8;
+  if (h->hop_real)
+    k_split_xhop<false><<<blocks, 256, 0, st>>>((long long)nslots, h->d_hop.p, (const double*)h->d_dx.p,
+                                                h->d_xhop_df.p);
+  else
+    k_split_xhop<true><<<blocks, 256, 0, st>>>((long long)nslots, h->d_hop.p, (const double*)h->d_dx.p,
+                                               h->d_xhop_df.p);
+  check_launch("k_split_xhop");
+  h->dfx_ready = true;
 }
 
 // elements in flight per thread in the l = r rows (two, within 85 registers, up
@@ -1225,11 +1243,195 @@ void gqt::launch_moments(gqt_ham* h, const void* l, const void* r, int R, int M,
 
 // ====================================================================== evolution core
 
+// Evolution orders of FP64 handles with one vector on the FP32 pipes (pairs of
+// FP32 numbers, gqt_df.cuh), when their moment rows run there too (FP64
+// arithmetic mode 1): the wavefront table and neighbour counts of the pair rows.
+static bool df_evo_applies(const gqt_ham* h, int R) {
+  return h->prec == GQT_FP64 && h->fp64_arith == 1 && R == 1 && h->variant != 0 && h->threads <= 256 &&
+         (h->K == 2 || h->K == 3 || h->K == 4 || h->K == 6) && h->d_dx.p != nullptr;
+}
+
+// An expansion coefficient as pairs (re.hi, re.lo, im.hi, im.lo).
+static float4 coef_df(double2 c) {
+  const float a = (float)c.x, b = (float)c.y;
+  return make_float4(a, (float)(c.x - (double)a), b, (float)(c.y - (double)b));
+}
+
+template <class F>
+static void df_dispatch(const gqt_ham* h, F&& f) {
+  auto kk = [&](auto ch) {
+    switch (h->K) {
+      case 2: f(ch, std::integral_constant<int, 2>()); break;
+      case 3: f(ch, std::integral_constant<int, 3>()); break;
+      case 4: f(ch, std::integral_constant<int, 4>()); break;
+      default: f(ch, std::integral_constant<int, 6>()); break;
+    }
+  };
+  if (h->hop_real)
+    kk(std::integral_constant<bool, false>());
+  else
+    kk(std::integral_constant<bool, true>());
+}
+
+static int occupancy_of(const void* f, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  return std::max(1, n);
+}
+
+template <int NSET>
+static void launch_evolve_df(gqt_ham* h, void* const* psi, const std::vector<double2>& c, cudaStream_t st,
+                             double* d_norms) {
+  ensure_df(h, st);
+  const int Np = (int)c.size();
+  const size_t smem = (size_t)NSET * (h->threads / 32) * sizeof(double) + 16;
+  int occ = h->blocks_per_sm;
+  if (occ <= 0)
+    df_dispatch(h, [&](auto ch, auto kk) {
+      occ = occupancy_of((const void*)k_evolve_df<decltype(ch)::value, decltype(kk)::value, NSET, 1>, h->threads,
+                         smem);
+    });
+  const BlockTable& T = h->table(1, occ);
+  const int nb = T.nblocks;
+  const size_t vb = h->vec_bytes(1);
+  float4* W1[NSET];
+  float4* W2[NSET];
+  float4* ACC[NSET];
+  for (int q = 0; q < NSET; ++q) {
+    W1[q] = (float4*)h->ws(WS_E1 + 2 * q, vb).p;
+    W2[q] = (float4*)h->ws(WS_E1 + 2 * q + 1, vb).p;
+    ACC[q] = (float4*)h->ws(WS_ACC0 + q, vb).p;
+  }
+  double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)(2 * NSET) * nb * sizeof(double2)).p;
+  const std::string key = key_of("evodf", {psi[0], psi[NSET - 1], W1[0], W2[0], ACC[0], partial, d_norms, T.d_blk.p},
+                                 {(double)NSET, (double)Np, (double)h->threads, (double)nb}) + coef_bits(c);
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    df_dispatch(h, [&](auto ch, auto kk) {
+      constexpr bool CH = decltype(ch)::value;
+      constexpr int KK = decltype(kk)::value;
+      const DfEll<CH> H = df_ell_of<CH>(h);
+      const int4* tab = (const int4*)T.d_tab4.p;
+      DfEvo<NSET> A;
+      for (int q = 0; q < NSET; ++q) {
+        A.psi[q] = (double2*)psi[q];
+        A.t1[q] = nullptr;
+        A.t2[q] = nullptr;
+        A.out[q] = W1[q];
+        A.t0[q] = W2[q];
+        A.acc[q] = ACC[q];
+      }
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      k_evolve_df<CH, KK, NSET, 0><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[0]),
+                                                                 Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
+      check_launch("k_evolve_df(0)");
+      if (Np <= 2) {
+        k_evolve_df<CH, KK, NSET, 3><<<nb, h->threads, smem, s2>>>(H, tab, A, zero, zero, partial, nb, NSET);
+        check_launch("k_evolve_df(3)");
+        return;
+      }
+      for (int m = 2; m < Np; ++m) {
+        for (int q = 0; q < NSET; ++q) {
+          A.t1[q] = (m - 1) % 2 == 1 ? W1[q] : W2[q];
+          A.out[q] = (m % 2 == 1) ? W1[q] : W2[q];
+          A.t2[q] = A.out[q];
+        }
+        size_t pe = prof_begin(s2);
+        if (m == Np - 1)
+          k_evolve_df<CH, KK, NSET, 2><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb, NSET);
+        else
+          k_evolve_df<CH, KK, NSET, 1><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb, NSET);
+        check_launch("k_evolve_df");
+        prof_end(pe, 1 + NSET, s2);
+      }
+    });
+    k_norm_check<<<1, 256, 0, s2>>>(partial, NSET, nb, 1, (const int*)T.d_seg_blk.p, h->nseg, 1e-10, d_norms,
+                                    (int*)h->d_flag.p);
+    check_launch("k_norm_check");
+  });
+}
+
+static void launch_msd_df(gqt_ham* h, void* p, void* px, const std::vector<double2>& c, cudaStream_t st) {
+  ensure_df(h, st);
+  ensure_df_x(h, st);
+  const int Np = (int)c.size();
+  const size_t smem = (size_t)2 * (h->threads / 32) * sizeof(double) + 16;
+  int occ = h->blocks_per_sm;
+  if (occ <= 0)
+    df_dispatch(h, [&](auto ch, auto kk) {
+      occ = occupancy_of((const void*)k_msd_evolve_df<decltype(ch)::value, decltype(kk)::value, 1>, h->threads,
+                         smem);
+    });
+  const BlockTable& T = h->table(1, occ);
+  const int nb = T.nblocks;
+  const size_t vb = h->vec_bytes(1);
+  float4* U1 = (float4*)h->ws(WS_E1, vb).p;
+  float4* U2 = (float4*)h->ws(WS_E1 + 1, vb).p;
+  float4* Z1 = (float4*)h->ws(WS_E1 + 2, vb).p;
+  float4* Z2 = (float4*)h->ws(WS_E1 + 3, vb).p;
+  float4* AP = (float4*)h->ws(WS_ACC0, vb).p;
+  float4* AX = (float4*)h->ws(WS_ACC0 + 1, vb).p;
+  double2* partial = (double2*)h->ws(WS_PARTIAL_EVO, (size_t)4 * nb * sizeof(double2)).p;
+  const std::string key = key_of("msddf", {p, px, U1, Z1, AP, AX, partial, T.d_blk.p},
+                                 {(double)Np, (double)h->threads, (double)nb}) + coef_bits(c);
+  run_graph(h, key, st, [&](cudaStream_t s2) {
+    df_dispatch(h, [&](auto ch, auto kk) {
+      constexpr bool CH = decltype(ch)::value;
+      constexpr int KK = decltype(kk)::value;
+      const DfEll<CH> H = df_ell_of<CH>(h);
+      const int4* tab = (const int4*)T.d_tab4.p;
+      DfMsd B;
+      B.p = (double2*)p;
+      B.px = (double2*)px;
+      B.u1 = B.u2 = B.z1 = B.z2 = nullptr;
+      B.uo = U1;
+      B.zo = Z1;
+      B.u0 = U2;
+      B.z0 = Z2;
+      B.accp = AP;
+      B.accx = AX;
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      k_msd_evolve_df<CH, KK, 0><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[0]),
+                                                               Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
+      check_launch("k_msd_evolve_df(0)");
+      if (Np <= 2) {
+        k_msd_evolve_df<CH, KK, 3><<<nb, h->threads, smem, s2>>>(H, tab, B, zero, zero, partial, nb, 2);
+        check_launch("k_msd_evolve_df(3)");
+        return;
+      }
+      for (int m = 2; m < Np; ++m) {
+        B.u1 = (m - 1) % 2 == 1 ? U1 : U2;
+        B.z1 = (m - 1) % 2 == 1 ? Z1 : Z2;
+        B.uo = (m % 2 == 1) ? U1 : U2;
+        B.zo = (m % 2 == 1) ? Z1 : Z2;
+        B.u2 = B.uo;
+        B.z2 = B.zo;
+        size_t pe = prof_begin(s2);
+        if (m == Np - 1)
+          k_msd_evolve_df<CH, KK, 2><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb, 2);
+        else
+          k_msd_evolve_df<CH, KK, 1><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb, 2);
+        check_launch("k_msd_evolve_df");
+        prof_end(pe, 4, s2);
+      }
+    });
+    k_norm_check_msd<<<1, 256, 0, s2>>>(partial, nb, 1, (const int*)T.d_seg_blk.p, h->nseg, 1e-10,
+                                        (int*)h->d_flag.p);
+    check_launch("k_norm_check_msd");
+  });
+}
+
 // In-place evolution of NSET vector sets (each [n][R]) by U(sign*dt) with Np
 // orders.  Norms before/after are checked on the device against tol.
 template <int NSET>
 static void launch_evolve_sets(gqt_ham* h, void* const* psi, int R, const std::vector<double2>& c, cudaStream_t st,
                                double* d_norms /* [nseg][R][2*NSET] or null */) {
+  if (df_evo_applies(h, R)) {
+    launch_evolve_df<NSET>(h, psi, c, st, d_norms);
+    return;
+  }
   const int Np = (int)c.size();
   const BlockTable& T = h->table(R);
   const int nb = T.nblocks, rs = rshift_of(R);
@@ -1294,6 +1496,10 @@ static void launch_evolve_sets(gqt_ham* h, void* const* psi, int R, const std::v
 }
 
 static void launch_msd_step(gqt_ham* h, void* p, void* px, int R, const std::vector<double2>& c, cudaStream_t st) {
+  if (df_evo_applies(h, R)) {
+    launch_msd_df(h, p, px, c, st);
+    return;
+  }
   const int Np = (int)c.size();
   const BlockTable& T = h->table(R);
   const int nb = T.nblocks, rs = rshift_of(R);

@@ -115,6 +115,8 @@ struct gqt_ham {
   int fp64_arith = 1;       // FP64 handles' R = 1 moment rows: 0 FP64 pipe, 1 pairs of FP32 (gqt_set_fp64_arith)
   gqt::DevBuf d_hop_df, d_diag_df;  // 2H~ and 2U/dE as (hi, lo) FP32 pairs, split on first use
   bool df_ready = false;
+  gqt::DevBuf d_xhop_df;  // -dx 2H~ (2[X,H~] slot values) as pairs, for the commutator orders
+  bool dfx_ready = false;
   // honeycomb cell layout recognised at build (site 2(c1 + L1 c2) + s; 0 = not that
   // layout) and, per sublattice and ELL slot, the neighbour type; enables the
   // temporally blocked rows (gqt_set_temporal_blocking)

@@ -94,6 +94,73 @@ def test_df_and_fp64_modes_agree(name):
         assert nerr(rows[1][k], rows[0][k]) < 1e-12
 
 
+@pytest.mark.parametrize("name", list(MODELS))
+@pytest.mark.parametrize("dt,sign", [(0.01, 1), (0.05, -1), (0.4, 1), (2.0, -1)])
+def test_df_evolution_matches_oracle_and_fp64_pipe(name, dt, sign):
+    """U(+-dt) psi (Eq. 17) and [X,U(dt)] psi (Eqs. 18, 22, 24) with the orders on
+    pairs of FP32 numbers (mode 1), for expansions of 1, 2, 3 and up to 29 orders,
+    on every neighbour count and with complex hoppings: within 1e-10 of the oracle,
+    within 1e-13 (U) and 1e-12 ([X,U]) of the FP64-pipe kernels (mode 0), and the
+    reported norm within 1e-12 of 1."""
+    lat, dE = MODELS[name]()
+    h = O.Hamiltonian(lat, dE)
+    psi = S.random_phase(lat.n, 1, seed=31)
+    rule = O.np_rule(dE * dt, 64)
+    for Np in sorted({1, 2, 3, rule}):
+        got = {}
+        for mode in (1, 0):
+            ham = _ham(lat, dE, mode)
+            d = torch.from_numpy(psi).cuda()
+            norm = np.full(1, np.nan)
+            errs = []
+            # an expansion cut below the rule fails the norm check (GQT_ENORM) after
+            # computing the truncated sum, which is still compared
+            try:
+                g.gqt_evolve(ham, d, 1, dt, sign, Np, norm=norm)
+            except g.GqtError as e:
+                errs.append(e.status)
+            out = torch.empty_like(d)
+            try:
+                g.gqt_commutator_evolve(ham, torch.from_numpy(psi).cuda(), out, 1, dt, Np)
+            except g.GqtError as e:
+                errs.append(e.status)
+            got[mode] = (d.cpu().numpy()[:, 0], out.cpu().numpy()[:, 0], norm[0], errs)
+        assert got[1][3] == got[0][3], (Np, got[1][3], got[0][3])
+        assert (len(got[1][3]) == 0) == (Np >= rule), (Np, rule, got[1][3])
+        assert nerr(got[1][0], h.evolve(psi[:, 0], dt, sign, Np)) < TOL64, Np
+        assert nerr(got[1][1], h.commutator_evolve(psi[:, 0], dt, Np)) < TOL64, Np
+        assert nerr(got[1][0], got[0][0]) < 1e-13, Np
+        assert nerr(got[1][1], got[0][1]) < 1e-12, Np
+        if Np >= rule:
+            assert abs(got[1][2] - 1.0) < 1e-12
+
+
+def test_df_evolution_runs_on_the_fp32_pipes():
+    """Mode 1 handles launch the paired-FP32 evolution orders (profile families 3
+    and 4 count the middle orders), and a VAC + MSD step of the bench workload's
+    form equals the FP64-pipe mode within 1e-12."""
+    lat, dE = MODELS["honeycomb37x23"]()
+    phi = torch.from_numpy(S.random_phase(lat.n, 1, seed=33)).cuda()
+    M = 64
+    rows = {}
+    for mode in (1, 0):
+        ham = _ham(lat, dE, mode)
+        a, b, p, px = (torch.empty_like(phi) for _ in range(4))
+        g.gqt_vac_init(ham, phi, a, b, 1)
+        g.gqt_msd_init(ham, phi, p, px, 1)
+        vac = np.empty((2, 1, 1, M))
+        msd = np.empty((2, 1, 1, M))
+        g.gqt_profile_start()
+        g.gqt_vac_moments(ham, a, b, 1, [0.74, 0.74], M, vac)
+        g.gqt_msd_moments(ham, p, px, 1, [0.74, 0.74], M, msd)
+        torch.cuda.synchronize()
+        _, n = g.gqt_profile_stop(5)
+        assert n[3] > 0 and n[4] > 0, n
+        rows[mode] = (vac.ravel(), msd.ravel(), a.cpu().numpy(), px.cpu().numpy())
+    for k in range(4):
+        assert nerr(rows[1][k], rows[0][k]) < 1e-12, k
+
+
 def test_df_ragged_segments_match_separate_builds():
     """Several segments in one handle (block-diagonal realisations): per-segment DOS
     and VAC moments equal the oracle on each realisation."""
