@@ -102,20 +102,16 @@ def _peaks():
 
 def measured_traffic(family: str, n_orbitals: int):
     """Per-launch DRAM traffic of a moment-kernel family scaled to n_orbitals, from
-    the committed ncu capture; None when the kernel source changed since."""
+    the committed ncu capture; None when any of its kernel sources changed since."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_moment_kernels.json")) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, d["kernel_source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != d["kernel_source_sha256"]:
-                return None
         fam = d["families"][family]
-        src = fam.get("kernel_source", d["kernel_source"])
-        sha = fam.get("kernel_source_sha256", d["kernel_source_sha256"])
-        with open(os.path.join(ROOT, src), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != sha:
-                return None
+        for src, sha in fam["kernel_sources"].items():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != sha:
+                    return None
         return (fam["dram_read_bytes"] + fam["dram_write_bytes"]) / fam["n_orbitals"] * n_orbitals
     except (OSError, KeyError, ValueError):
         return None
@@ -152,12 +148,13 @@ def bytes_per_orbital_pair(K: int, hop_real: bool, R: int) -> float:
     return 6 * 16 * R + K * (4 + (8 if hop_real else 16)) + 8
 
 
-def bytes_per_orbital_tiled(K: int, hop_real: bool, pair: bool) -> float:
+def bytes_per_orbital_tiled(K: int, hop_real: bool, pair: bool, uniform: bool = False) -> float:
     """Algorithmic bytes per orbital per launch of the temporally blocked kernel
     (two orders): per chain T_m and T_{m-1} read and T_{m+1}, T_{m+2} written
     (4 complex FP64-sized values), H~ once per site (K hoppings and the
-    diagonal as FP32 pairs, no index array)."""
-    return (2 if pair else 1) * 4 * 16 + K * (8 if hop_real else 16) + 8
+    diagonal as FP32 pairs, no index array; no hoppings either when they all
+    hold one value)."""
+    return (2 if pair else 1) * 4 * 16 + (0 if uniform else K * (8 if hop_real else 16)) + 8
 
 
 def fp64_fma_per_orbital(K: int, hop_real: bool, dot: str) -> int:
@@ -169,14 +166,19 @@ def fp64_fma_per_orbital(K: int, hop_real: bool, dot: str) -> int:
     return {"re": rec + 2, "dbl": rec + 4, "pair": 2 * rec + 4}[dot]
 
 
-def df_fp32_ops_per_orbital(K: int, hop_real: bool, kind: str) -> int:
+def df_fp32_ops_per_orbital(K: int, hop_real: bool, kind: str, uniform: bool = False) -> int:
     """FP32-pipe instructions per orbital per launch of the paired-FP32 kernels: one
     pair multiply-accumulate (TwoProduct by FMA, three FMAs for the low parts, TwoSum
     and two adds) is 12; a recurrence takes 2 of them per real diagonal or
     neighbour term on each of Re, Im (4 for complex hoppings) and two 6-instruction
-    renormalisations; each Re dot takes 2 (24 instructions).  The l = r kernel runs
-    one recurrence and two dots, the two-recurrence kernel two and two."""
-    rec = 12 * (2 + K * (2 if hop_real else 4)) + 12
+    renormalisations; each Re dot takes 2 (24 instructions).  With one common
+    hopping a recurrence instead sums the K neighbour pairs (K - 1 pair additions
+    of 8 on each of Re, Im) before two multiply-accumulates per part.  The l = r
+    kernel runs one recurrence and two dots, the two-recurrence kernel two and two."""
+    if uniform:
+        rec = 2 * (8 * (K - 1) + 2 * 12) + 12
+    else:
+        rec = 12 * (2 + K * (2 if hop_real else 4)) + 12
     return {"dbl": rec + 48, "pair": 2 * rec + 48, "re": rec + 24}[kind]
 
 
@@ -585,6 +587,7 @@ def run_ours(args):
     hbm, peak_kind = _peaks()
     df = args.fp64_arith == 1
     sfx = "_df" if df else ""
+    uniform = bool(ham.forms & g.GQT_FORM_UNIFORM_HOP)
     fam = {1: ("k_cheb_re (VAC row: fused SpMV + three-term recurrence + Re <l|T_m|r>)",
                bytes_per_orbital_cheb(3, True, ham.hop_real, R), "re", 1),
            5: (f"k_cheb_dbl{sfx} (MSD row: fused SpMV + recurrence + <u_n|u_n>, <u_n+1|u_n>)",
@@ -592,9 +595,11 @@ def run_ours(args):
            6: (f"k_cheb_pair{sfx} (VAC row: two fused SpMV + recurrences, T_k l and T_k r, + Re <A_k|B_k>, "
                "Re <A_k|B_k+1>)", bytes_per_orbital_pair(3, ham.hop_real, R), "pair", 1),
            10: ("k_cheb2_honey_df_pair (VAC row, temporally blocked: two steps of both recurrences per launch, "
-                "the second from the first's rows in L2)", bytes_per_orbital_tiled(3, ham.hop_real, True), "pair", 2),
-           11: ("k_cheb2_honey_df_dbl (MSD row, temporally blocked: two steps per launch)",
-                bytes_per_orbital_tiled(3, ham.hop_real, False), "dbl", 2)}
+                "the second from the first's rows in L2" + (", one common hopping" if uniform else "") + ")",
+                bytes_per_orbital_tiled(3, ham.hop_real, True, uniform), "pair", 2),
+           11: ("k_cheb2_honey_df_dbl (MSD row, temporally blocked: two steps per launch"
+                + (", one common hopping" if uniform else "") + ")",
+                bytes_per_orbital_tiled(3, ham.hop_real, False, uniform), "dbl", 2)}
     total_prof = float(np.sum(prof_ms))
     dom = max(fam, key=lambda k: prof_ms[k])
     fams = {}
@@ -605,7 +610,7 @@ def run_ours(args):
                                  "achieved_gbs": N * bpo_k / avg / 1e9 if nl else None,
                                  "share_of_timed_kernels": prof_ms[k] / max(total_prof, 1e-12)}
     kname, bpo, fkind, nsteps = fam[dom]
-    traffic = measured_traffic(kname.split()[0], N)
+    traffic = measured_traffic(kname.split()[0] + ("_uh" if uniform and nsteps == 2 else ""), N)
     n_launch = int(prof_n[dom])
     avg_s = prof_ms[dom] * 1e-3 / max(n_launch, 1)
     achieved = N * bpo / avg_s / 1e9
@@ -618,7 +623,7 @@ def run_ours(args):
     if df:
         # arithmetic roofline of the paired-FP32 kernel: FP32-pipe instructions per
         # orbital against SMs x 128 lanes x the SM clock sampled during the timed region
-        ops = df_fp32_ops_per_orbital(3, ham.hop_real, fkind) * R * nsteps
+        ops = df_fp32_ops_per_orbital(3, ham.hop_real, fkind, uniform and nsteps == 2) * R * nsteps
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = float(clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0)
         fp32_peak = sms * 128 * mhz * 1e6 / 1e9
@@ -659,7 +664,8 @@ def run_ours(args):
                    "vectors_per_gpu": R, "bessel_orders": Np, "dt_hbar_per_eV": w.dt, "energies": int(E.numel()),
                    "step": "one VAC + MSD time step (2M moments, 2 evolutions) + KPM reconstruction",
                    "temporal_blocking": bool(args.temporal_blocking),
-                   "hop_storage": "real FP64" if ham.hop_real else "complex FP64",
+                   "hop_storage": ("real FP64" if ham.hop_real else "complex FP64")
+                   + ("; one common hopping (blocked rows read no hop array)" if uniform else ""),
                    "arith": ("moment rows on pairs of FP32 numbers (double-float, ~48-bit significands; FP64 "
                              "storage, results within 1e-12 of the FP64 mode), evolution in FP64")
                    if df else "FP64 fused multiply-adds",

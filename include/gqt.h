@@ -122,6 +122,22 @@ gqt_status gqt_generate_lattice(const gqt_lattice* lattice, int64_t* n, int* K, 
 gqt_status gqt_ham_info(const gqt_ham* ham, int64_t* n, double* energy_scale, double* volume, int* nseg,
                         int* precision, int* hop_real);
 
+/* Storage forms the handle's rows can take, recognised when it is built (and
+ * after gqt_update_hamiltonian), as bits of *flags:
+ *   GQT_FORM_HONEYCOMB (1): the neighbour lists follow the built-in honeycomb
+ *     cell layout (the temporally blocked rows, gqt_set_temporal_blocking);
+ *   GQT_FORM_UNIFORM_HOP (2): FP64 handle whose slots all hold one real hopping
+ *     (the Anderson form, disorder on the sites only): its blocked rows read no
+ *     hop array and sum each row's neighbour values before one product;
+ *   GQT_FORM_CUBIC_SWEEP (4): built-in simple-cubic lattice with the blocked
+ *     sweep order (gqt_set_sweep_order).
+ * The forms change the arithmetic order only; results agree with the general
+ * kernels to rounding.  EINVAL on a null handle or flags. */
+#define GQT_FORM_HONEYCOMB 1
+#define GQT_FORM_UNIFORM_HOP 2
+#define GQT_FORM_CUBIC_SWEEP 4
+gqt_status gqt_ham_forms(const gqt_ham* ham, int* flags);
+
 /* Random-phase vectors (Sec. 3.1, Eq. 13): phi[i*R + r] = exp(i 2 pi u)/sqrt(n_s),
  * u = top 53 bits of draw i of SplitMix64 stream (2^20 + first_vector + r) of
  * seed / 2^53, n_s = sites of i's segment.  d_phi: device, [n][R], the

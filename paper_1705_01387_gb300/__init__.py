@@ -18,6 +18,7 @@ from .build import LIB, build
 GQT_OK, GQT_EINVAL, GQT_ENOMEM, GQT_ECUDA, GQT_ERANGE, GQT_ENORM, GQT_ENAN, GQT_ETIMEOUT = range(8)
 GQT_FP64, GQT_FP32_ACC64 = 0, 1
 GQT_LATTICE_CUSTOM, GQT_LATTICE_CHAIN, GQT_LATTICE_SQUARE, GQT_LATTICE_HONEYCOMB, GQT_LATTICE_CUBIC = range(5)
+GQT_FORM_HONEYCOMB, GQT_FORM_UNIFORM_HOP, GQT_FORM_CUBIC_SWEEP = 1, 2, 4
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ERANGE", "ENORM", "ENAN", "ETIMEOUT"]
 
 
@@ -44,6 +45,7 @@ _SIGS = {
     "gqt_update_hamiltonian": [_P, _P, _P, _P],
     "gqt_generate_lattice": [C.POINTER(gqt_lattice), _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "gqt_ham_info": [_P, _P, _P, _P, _P, _P, _P],
+    "gqt_ham_forms": [_P, _P],
     "gqt_random_phase": [_P, _U64, _I, _I, _P, _P],
     "gqt_cheb_moments": [_P, _P, _P, _I, _I, _P, _P],
     "gqt_dos_moments": [_P, _P, _I, _I, _P, _P],
@@ -165,6 +167,14 @@ class Ham:
                                   C.byref(real)))
         self.n, self.energy_scale, self.volume = n.value, dE.value, vol.value
         self.nseg, self.precision, self.hop_real = nseg.value, prec.value, bool(real.value)
+
+    @property
+    def forms(self) -> int:
+        """Bits of GQT_FORM_HONEYCOMB, GQT_FORM_UNIFORM_HOP, GQT_FORM_CUBIC_SWEEP
+        (gqt_ham_forms), read when asked (updates can change them)."""
+        f = C.c_int()
+        _check(lib().gqt_ham_forms(self.ptr, C.byref(f)))
+        return f.value
 
     @property
     def complex_dtype(self):

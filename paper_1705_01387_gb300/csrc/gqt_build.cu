@@ -401,6 +401,9 @@ extern "C" gqt_status gqt_build_hamiltonian(const gqt_lattice* lattice, double e
       upload(h->d_hop, hop.data(), hop.size() * 8);
       upload(h->d_diag, dg.data(), dg.size() * 8);
       upload(h->d_dx, dxv.data(), dxv.size() * 8);
+      h->hop_uniform = hop_real && !hop.empty() &&
+                       std::all_of(hop.begin(), hop.end(), [&](double v) { return v == hop[0]; });
+      h->hop0 = h->hop_uniform ? hop[0] : 0.0;
     } else {
       std::vector<float> hop(n * K * hw), dg(n), dxv(n * K);
       for (int64_t i = 0; i < n; ++i) {
@@ -550,6 +553,12 @@ extern "C" gqt_status gqt_update_hamiltonian(gqt_ham* h, const double* onsite, c
       put(h->d_diag, dg.data(), dg.size() * 8);
       h->df_ready = false;  // the (hi, lo) split of 2H~ is taken again on next use
       h->dfx_ready = false;
+      h->hop_uniform = hw == 1 && !hop.empty() &&
+                       std::all_of(hop.begin(), hop.end(), [&](double v) { return v == hop[0]; });
+      h->hop0 = h->hop_uniform ? hop[0] : 0.0;
+      for (auto& gr : h->graphs) cudaGraphExecDestroy(gr.second);  // the blocked rows may switch form
+      h->graphs.clear();
+      h->graph_data.clear();
     } else {
       std::vector<float> hop(n * K * hw), dg(n);
       for (int64_t i = 0; i < n; ++i) {

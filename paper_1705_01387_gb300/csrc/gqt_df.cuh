@@ -48,6 +48,7 @@ struct DfEll {
   const typename DfHop<CH>::T* hop = nullptr;  // [K][n]
   const float2* diag = nullptr;                // [n]
   const typename DfHop<CH>::T* xhop = nullptr;  // [K][n] 2[X,H~]_ij = -dx_ij 2H~_ij (commutator orders)
+  float2 h0 = {0.f, 0.f};  // the common 2H~_ij of handles whose slots all hold one real hopping
 };
 
 // ---------------------------------------------------------------- pair arithmetic
@@ -184,6 +185,33 @@ __device__ __forceinline__ float4 df_step(const typename DfHop<CH>::T (&hv)[KK],
 #pragma unroll
   for (int k = 0; k < KK; ++k) dfc_mac(a, hv[k], nb[k]);
   return dfc_out(a, FIRST);
+}
+
+// (sh, sl) += (bh, bl) for pairs, unnormalised (TwoSum of the high words, the
+// low words and the TwoSum error added into sl).
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  const float s = __fadd_rn(sh, bh);
+  const float v = __fsub_rn(s, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(bh, v));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(bl, t));
+}
+
+// T_m at one element when every hopping equals h0 (a real 2H~ value): the
+// neighbour values are summed first, so one product with h0 replaces KK.
+template <int KK>
+__device__ __forceinline__ float4 df_step_uh(float2 h0, float2 dg, float4 own, const float4 (&nb)[KK], float4 tm2) {
+  float rh = nb[0].x, rl = nb[0].y, ih = nb[0].z, il = nb[0].w;
+#pragma unroll
+  for (int k = 1; k < KK; ++k) {
+    df_add(rh, rl, nb[k].x, nb[k].y);
+    df_add(ih, il, nb[k].z, nb[k].w);
+  }
+  DfC a = dfc_neg(tm2);
+  dfc_mac(a, dg, own);
+  df_mac(a.rh, a.rl, h0.x, h0.y, rh, rl);
+  df_mac(a.ih, a.il, h0.x, h0.y, ih, il);
+  return dfc_out(a, false);
 }
 
 // VAC rows by two recurrences (the pair form of k_cheb_pair_w): chain A from l,

@@ -724,6 +724,10 @@ static DfEll<CH> df_ell_of(const gqt_ham* h) {
   e.hop = (const typename DfHop<CH>::T*)h->d_hop_df.p;
   e.diag = (const float2*)h->d_diag_df.p;
   e.xhop = (const typename DfHop<CH>::T*)h->d_xhop_df.p;
+  if (h->hop_uniform) {
+    const float a = (float)h->hop0;
+    e.h0 = make_float2(a, (float)(h->hop0 - (double)a));
+  }
   return e;
 }
 
@@ -848,14 +852,22 @@ static void df_rows(gqt_ham* h, const BlockTable& T, bool pair, int steps, const
         const bool fold = tgrid > nb;
         double2* pout = fold ? tscratch : partial + (size_t)(2 * m - 2) * nb;
         const int ostride = fold ? tgrid : nb, nzero = fold ? 0 : nb;
-        if (pair)
-          k_cheb2_honey_df<CH, 2><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, A[cur], A[prv], B[cur], B[prv],
-                                                                 A[f[0]], A[f[1]], B[f[0]], B[f[1]], pout, ostride,
-                                                                 nzero);
+        // handles whose slots all hold one real hopping read no hop array (UH)
+        auto blocked = [&](auto uh) {
+          constexpr bool UH = decltype(uh)::value && !CH;
+          if (pair)
+            k_cheb2_honey_df<CH, 2, UH><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, A[cur], A[prv], B[cur],
+                                                                       B[prv], A[f[0]], A[f[1]], B[f[0]], B[f[1]],
+                                                                       pout, ostride, nzero);
+          else
+            k_cheb2_honey_df<CH, 1, UH><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, B[cur], B[prv], nullptr,
+                                                                       nullptr, B[f[0]], B[f[1]], nullptr, nullptr,
+                                                                       pout, ostride, nzero);
+        };
+        if (h->hop_uniform)
+          blocked(std::true_type());
         else
-          k_cheb2_honey_df<CH, 1><<<tgrid, 2 * bw, TL_SMEM, s2>>>(H, G, bw, tnseg, B[cur], B[prv], nullptr, nullptr,
-                                                                 B[f[0]], B[f[1]], nullptr, nullptr, pout, ostride,
-                                                                 nzero);
+          blocked(std::false_type());
         check_launch("k_cheb2_honey_df");
         if (fold) {
           k_tl_fold<<<4, 128, 0, s2>>>(tscratch, tgrid, 1, partial, nb, 2 * m - 2);
@@ -1715,6 +1727,14 @@ gqt_status gqt_ham_info(const gqt_ham* h, int64_t* n, double* energy_scale, doub
   if (nseg) *nseg = h->nseg;
   if (precision) *precision = h->prec;
   if (hop_real) *hop_real = h->hop_real ? 1 : 0;
+  API_END
+}
+
+gqt_status gqt_ham_forms(const gqt_ham* h, int* flags) {
+  API_BEGIN
+  require(h != nullptr && flags != nullptr, "gqt_ham_forms: null argument");
+  *flags = (h->honey_L1 > 0 ? GQT_FORM_HONEYCOMB : 0) | (h->hop_uniform ? GQT_FORM_UNIFORM_HOP : 0) |
+           (h->row_shift > 0 ? GQT_FORM_CUBIC_SWEEP : 0);
   API_END
 }
 

@@ -93,6 +93,10 @@ struct gqt_ham {
   int K = 0;
   gqt_precision prec = GQT_FP64;
   bool hop_real = true;
+  // every ELL slot holds the same real hopping (FP64 handles; the Anderson form:
+  // disorder on the sites only): its 2H~ value, used by the blocked rows
+  bool hop_uniform = false;
+  double hop0 = 0.0;
   double dE = 1.0;
   double volume = 0.0;
   double length_x = 0.0;

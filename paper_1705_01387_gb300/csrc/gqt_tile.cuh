@@ -83,12 +83,14 @@ struct TlSite {
 
 // Loads for site i with neighbours j[3]: in = the order the step multiplies,
 // pv = the order before.
-template <bool CH, int NC, bool IN_RO>
+template <bool CH, int NC, bool IN_RO, bool UH = false>
 __device__ __forceinline__ void tl_load(TlSite<CH, NC>& S, const DfEll<CH>& H, int i, const int (&j)[3],
                                         const float4* in0, const float4* in1, const float4* __restrict__ pv0,
                                         const float4* __restrict__ pv1) {
+  if (!UH) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) S.hv[k] = __ldg(H.hop + (size_t)k * H.n + i);
+    for (int k = 0; k < 3; ++k) S.hv[k] = __ldg(H.hop + (size_t)k * H.n + i);
+  }
   S.dg = __ldg(H.diag + i);
 #pragma unroll
   for (int ch = 0; ch < NC; ++ch) {
@@ -100,10 +102,16 @@ __device__ __forceinline__ void tl_load(TlSite<CH, NC>& S, const DfEll<CH>& H, i
   }
 }
 
-template <bool CH, int NC>
-__device__ __forceinline__ void tl_compute(const TlSite<CH, NC>& S, float4 (&v)[NC]) {
+// UH: every hopping is the real value H.h0 (no hop array is read).
+template <bool CH, int NC, bool UH = false>
+__device__ __forceinline__ void tl_compute(const TlSite<CH, NC>& S, const DfEll<CH>& H, float4 (&v)[NC]) {
 #pragma unroll
-  for (int ch = 0; ch < NC; ++ch) v[ch] = df_step<CH, 3, false>(S.hv, S.dg, S.own[ch], S.nb[ch], S.prev[ch]);
+  for (int ch = 0; ch < NC; ++ch) {
+    if (UH)
+      v[ch] = df_step_uh<3>(H.h0, S.dg, S.own[ch], S.nb[ch], S.prev[ch]);
+    else
+      v[ch] = df_step<CH, 3, false>(S.hv, S.dg, S.own[ch], S.nb[ch], S.prev[ch]);
+  }
 }
 
 // Dots of one order at an owned site: NC = 2, Re <A_k|B_k> and Re <A_k|B_k+1>;
@@ -150,7 +158,7 @@ struct TlCols {
 
 // Threads per CTA: two per cell of a band (one per site of a band row), at most
 // 256; three CTAs per SM (at most 85 registers).
-template <bool CH, int NC>
+template <bool CH, int NC, bool UH = false>
 __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
     DfEll<CH> H, Honey G, int bw, int nseg, const float4* __restrict__ xa, const float4* __restrict__ ya,
     const float4* __restrict__ xb, const float4* __restrict__ yb, float4* za, float4* __restrict__ wa, float4* zb,
@@ -183,9 +191,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
       int j[3];
       const int i = C.at(G, y0 - 1 + (q >> 1), j);
       TlSite<CH, NC> T;
-      tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
+      tl_load<CH, NC, true, UH>(T, H, i, j, xa, xb, ya, yb);
       float4 v[NC];
-      tl_compute<CH, NC>(T, v);
+      tl_compute<CH, NC, UH>(T, H, v);
       za[i] = v[0];
       if (NC == 2) zb[i] = v[NC - 1];
     }
@@ -196,9 +204,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
       int j[3];
       const int i = C.at(G, y0 - 1 + t, j);
       TlSite<CH, NC> T;
-      tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
+      tl_load<CH, NC, true, UH>(T, H, i, j, xa, xb, ya, yb);
       float4 v[NC];
-      tl_compute<CH, NC>(T, v);
+      tl_compute<CH, NC, UH>(T, H, v);
       za[i] = v[0];
       if (NC == 2) zb[i] = v[NC - 1];
       if (t >= 1 && t <= S) tl_dots<NC>(q0, q1, T.own, v);
@@ -208,9 +216,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
       int j[3];
       const int i = C.at(G, y0 + t - 3, j);
       TlSite<CH, NC> U;
-      tl_load<CH, NC, false>(U, H, i, j, za, zb, xa, xb);
+      tl_load<CH, NC, false, UH>(U, H, i, j, za, zb, xa, xb);
       float4 v[NC];
-      tl_compute<CH, NC>(U, v);
+      tl_compute<CH, NC, UH>(U, H, v);
       wa[i] = v[0];
       if (NC == 2) wb[i] = v[NC - 1];
       tl_dots<NC>(q2, q3, U.own, v);
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
             if (lane == 1) tl_prefetch_l2(ya + i0, vb);
             if (lane == 2) tl_prefetch_l2(xb + i0, vb);
             if (lane == 3) tl_prefetch_l2(yb + i0, vb);
-            if (lane >= 4 && lane < 7)
+            if (!UH && lane >= 4 && lane < 7)
               tl_prefetch_l2(H.hop + (size_t)(lane - 4) * H.n + i0,
                              (uint32_t)(nsite * sizeof(typename DfHop<CH>::T)));
             if (lane == 7) tl_prefetch_l2(H.diag + i0, (uint32_t)nsite * 8u);
@@ -258,9 +266,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
           int j[3];
           const int i = C.at(G, y0 - 1 + t, j);
           TlSite<CH, NC> T;
-          tl_load<CH, NC, true>(T, H, i, j, xa, xb, ya, yb);
+          tl_load<CH, NC, true, UH>(T, H, i, j, xa, xb, ya, yb);
           float4 v[NC];
-          tl_compute<CH, NC>(T, v);
+          tl_compute<CH, NC, UH>(T, H, v);
           za[i] = v[0];
           if (NC == 2) zb[i] = v[NC - 1];
           if (t >= 1 && t <= S) tl_dots<NC>(q0, q1, T.own, v);
@@ -269,9 +277,9 @@ __global__ void __launch_bounds__(256, 3) k_cheb2_honey_df(
           int j[3];
           const int i = C.at(G, y0 + t - 3, j);
           TlSite<CH, NC> U;
-          tl_load<CH, NC, false>(U, H, i, j, za, zb, xa, xb);
+          tl_load<CH, NC, false, UH>(U, H, i, j, za, zb, xa, xb);
           float4 v[NC];
-          tl_compute<CH, NC>(U, v);
+          tl_compute<CH, NC, UH>(U, H, v);
           wa[i] = v[0];
           if (NC == 2) wb[i] = v[NC - 1];
           tl_dots<NC>(q2, q3, U.own, v);

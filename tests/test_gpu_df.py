@@ -205,6 +205,61 @@ def test_df_split_follows_hamiltonian_updates():
     assert nerr(mu.ravel(), ref) < TOL64
 
 
+def test_blocked_rows_follow_hopping_uniformity_through_updates():
+    """A honeycomb handle whose hoppings are all equal runs the blocked rows without
+    reading a hop array (one product with the common value); an update to unequal
+    bond hoppings, and back to equal ones, switches the form on the same handle.
+    DOS and VAC rows match the oracle on each model, and the blocked kernel runs."""
+    lat, dE = TILED["honeycomb64x32"]()
+    ham = _ham(lat, dE)
+    phi = S.random_phase(lat.n, 1, seed=8)
+    d = torch.from_numpy(phi).cuda()
+    M = 40
+    dts = np.array([0.4])
+    Np = [O.np_rule(dE * 0.4, 64)]
+    t0 = lat.hop.copy()
+    j = lat.nb_idx
+    i = np.arange(lat.n)[:, None]
+    models = [t0, t0 * (1.0 + 0.05 * ((i + j) % 7) / 7.0), t0 * 0.9]  # equal, unequal (symmetric), equal
+    for q, hop in enumerate(models):
+        if q:
+            lat.hop = hop
+            g.gqt_update_hamiltonian(ham, lat.onsite, lat.hop)
+        uniform = g.GQT_FORM_UNIFORM_HOP if q != 1 else 0
+        assert ham.forms == g.GQT_FORM_HONEYCOMB | uniform, (q, ham.forms)
+        dos = np.empty((1, 1, M))
+        vac = np.empty((1, 1, 1, M))
+        a, b = torch.empty_like(d), torch.empty_like(d)
+        g.gqt_vac_init(ham, d, a, b, 1)
+
+        def run():
+            g.gqt_dos_moments(ham, d, 1, M, dos)
+            g.gqt_vac_moments(ham, a, b, 1, dts, M, vac, Np=Np)
+
+        assert _tiled_launches(run) > 0, q
+        h = O.Hamiltonian(lat, dE)
+        assert nerr(dos.ravel(), h.dos_moments(phi[:, 0], M).real) < TOL64, q
+        assert nerr(vac.ravel(), h.vac_moments(phi[:, 0], dts, Np, M)[0]) < TOL64, q
+
+
+def test_storage_forms_reported():
+    """gqt_ham_forms: the honeycomb cell layout, one common real hopping (FP64
+    handles) and the blocked cubic sweep order, as recognised at build."""
+    hc = S.honeycomb(64, 32, -2.7, 2.0, seed=13)
+    dE = S.energy_scale_rule(3, -2.7, 2.0)
+    assert g.gqt_build_hamiltonian(hc, dE).forms == g.GQT_FORM_HONEYCOMB | g.GQT_FORM_UNIFORM_HOP
+    assert g.gqt_build_hamiltonian(hc, dE, g.GQT_FP32_ACC64).forms == g.GQT_FORM_HONEYCOMB
+    vac = S.honeycomb(64, 32, -2.7, 2.0, seed=13, vacancy_frac=0.01)
+    assert g.gqt_build_hamiltonian(vac, dE).forms == g.GQT_FORM_HONEYCOMB
+    ph = S.with_random_bond_phases(hc, 5)
+    assert g.gqt_build_hamiltonian(ph, dE).forms == g.GQT_FORM_HONEYCOMB
+    cub = g.gqt_build_hamiltonian(None, S.energy_scale_rule(6, -1.0, 16.5), g.GQT_FP64, kind=g.GQT_LATTICE_CUBIC,
+                                  L1=64, t=-1.0, W=16.5, seed=3)
+    assert cub.forms == g.GQT_FORM_CUBIC_SWEEP | g.GQT_FORM_UNIFORM_HOP
+    sq = S.square(41, 29, -1.0, 4.0, seed=5)
+    assert g.gqt_build_hamiltonian(sq, S.energy_scale_rule(4, -1.0, 4.0)).forms == g.GQT_FORM_UNIFORM_HOP
+
+
 def test_df_mode_argument():
     lat, dE = MODELS["chain5001"]()
     ham = g.gqt_build_hamiltonian(lat, dE)
