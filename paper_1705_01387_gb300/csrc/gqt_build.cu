@@ -553,12 +553,18 @@ extern "C" gqt_status gqt_update_hamiltonian(gqt_ham* h, const double* onsite, c
       put(h->d_diag, dg.data(), dg.size() * 8);
       h->df_ready = false;  // the (hi, lo) split of 2H~ is taken again on next use
       h->dfx_ready = false;
-      h->hop_uniform = hw == 1 && !hop.empty() &&
+      const bool uni = hw == 1 && !hop.empty() &&
                        std::all_of(hop.begin(), hop.end(), [&](double v) { return v == hop[0]; });
-      h->hop0 = h->hop_uniform ? hop[0] : 0.0;
-      for (auto& gr : h->graphs) cudaGraphExecDestroy(gr.second);  // the blocked rows may switch form
-      h->graphs.clear();
-      h->graph_data.clear();
+      const double h0 = uni ? hop[0] : 0.0;
+      if (uni != h->hop_uniform || h0 != h->hop0) {
+        // the blocked rows switch form, or their common hopping (a kernel argument
+        // inside the captured graphs) changes: retire the graphs
+        for (auto& gr : h->graphs) cudaGraphExecDestroy(gr.second);
+        h->graphs.clear();
+        h->graph_data.clear();
+      }
+      h->hop_uniform = uni;
+      h->hop0 = h0;
     } else {
       std::vector<float> hop(n * K * hw), dg(n);
       for (int64_t i = 0; i < n; ++i) {
