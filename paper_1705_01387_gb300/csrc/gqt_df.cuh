@@ -1,4 +1,4 @@
-// gqt_df.cuh -- FP64-storage moment rows computed on the FP32 pipes.
+// gqt_df.cuh -- FP64-storage moment rows and evolution orders computed on the FP32 pipes.
 //
 // GB300 issues about 2 FP64 fused multiply-adds per clock per SM and 128 FP32
 // ones, so the FP64 moment kernels (k_cheb_pair_w, k_cheb_dbl_w) are bound by

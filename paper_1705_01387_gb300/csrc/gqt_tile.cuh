@@ -41,7 +41,14 @@
 // Arithmetic, dots and partial-sum slots are those of k_cheb_pair_df (NC = 2
 // chains, A from l and B from r) and k_cheb_dbl_df (NC = 1, l = r): the pass
 // over steps m and m + 1 adds the dots of moment slots 2m-2 .. 2m+1.  The
-// outputs go to buffers other than the inputs.
+// outputs go to buffers other than the inputs.  When every slot holds the same
+// real hopping (the Anderson form), the UH instances read no hop array and sum
+// a row's neighbour values before one product with it (136 and 72 bytes per
+// orbital instead of 160 and 96).
+//
+// The same walk serves FP32-storage handles with R = 2..16 vectors per site
+// (k_cheb2_honey_wv, below): G = R/2 lanes per site, FP32 arithmetic in the
+// single-order kernels' order, FP32 compensated dots per vector.
 #pragma once
 
 namespace gqt {
