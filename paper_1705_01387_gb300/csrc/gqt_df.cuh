@@ -197,21 +197,38 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl)
   sl = __fadd_rn(sl, __fadd_rn(bl, t));
 }
 
-// T_m at one element when every hopping equals h0 (a real 2H~ value): the
-// neighbour values are summed first, so one product with h0 replaces KK.
+// a += h0 * (sum_k nb[k]) for a real pair h0: the neighbour values are summed as
+// pairs first, so one product with h0 replaces KK.
 template <int KK>
-__device__ __forceinline__ float4 df_step_uh(float2 h0, float2 dg, float4 own, const float4 (&nb)[KK], float4 tm2) {
+__device__ __forceinline__ void dfc_mac_sum(DfC& a, float2 h0, const float4 (&nb)[KK]) {
   float rh = nb[0].x, rl = nb[0].y, ih = nb[0].z, il = nb[0].w;
 #pragma unroll
   for (int k = 1; k < KK; ++k) {
     df_add(rh, rl, nb[k].x, nb[k].y);
     df_add(ih, il, nb[k].z, nb[k].w);
   }
-  DfC a = dfc_neg(tm2);
-  dfc_mac(a, dg, own);
   df_mac(a.rh, a.rl, h0.x, h0.y, rh, rl);
   df_mac(a.ih, a.il, h0.x, h0.y, ih, il);
-  return dfc_out(a, false);
+}
+
+// T_m at one element when every hopping equals h0 (a real 2H~ value), as
+// df_step (T_1 = H~ T_0 when FIRST).
+template <int KK, bool FIRST = false>
+__device__ __forceinline__ float4 df_step_uh(float2 h0, float2 dg, float4 own, const float4 (&nb)[KK], float4 tm2) {
+  DfC a = FIRST ? dfc_zero() : dfc_neg(tm2);
+  dfc_mac(a, dg, own);
+  dfc_mac_sum<KK>(a, h0, nb);
+  return dfc_out(a, FIRST);
+}
+
+// T_m with the hoppings of the slots (hv) or, when UH, the common value H.h0.
+template <bool CH, int KK, bool FIRST, bool UH>
+__device__ __forceinline__ float4 df_step_any(const DfEll<CH>& H, const typename DfHop<CH>::T (&hv)[KK], float2 dg,
+                                              float4 own, const float4 (&nb)[KK], float4 tm2) {
+  if constexpr (UH)
+    return df_step_uh<KK, FIRST>(H.h0, dg, own, nb, tm2);
+  else
+    return df_step<CH, KK, FIRST>(hv, dg, own, nb, tm2);
 }
 
 // VAC rows by two recurrences (the pair form of k_cheb_pair_w): chain A from l,
@@ -382,19 +399,19 @@ struct DfEvo {
 __device__ __forceinline__ double2 df_to_d2(float4 f) { return make_double2(df_value(f.x, f.y), df_value(f.z, f.w)); }
 __device__ __forceinline__ DfC dfc_of(float4 a) { return DfC{a.x, a.y, a.z, a.w}; }
 
-template <bool CH, int KK>
+template <bool CH, int KK, bool UH = false>
 __device__ __forceinline__ void df_row_ops(const DfEll<CH>& H, int i, int (&idx)[KK],
                                            typename DfHop<CH>::T (&hv)[KK], float2& dg) {
 #pragma unroll
   for (int k = 0; k < KK; ++k) {
     const size_t s = (size_t)k * H.n + i;
     idx[k] = __ldg(H.idx + s);
-    hv[k] = __ldg(H.hop + s);
+    if (!UH) hv[k] = __ldg(H.hop + s);
   }
   dg = __ldg(H.diag + i);
 }
 
-template <bool CH, int KK, int NSET, int PH>
+template <bool CH, int KK, int NSET, int PH, bool UH = false>
 __global__ void __launch_bounds__(256) k_evolve_df(DfEll<CH> H, const int4* __restrict__ tab, DfEvo<NSET> A,
                                                    float4 c0, float4 c1, double2* __restrict__ partial, int nblocks,
                                                    int slot) {
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(256) k_evolve_df(DfEll<CH> H, const int4* __re
     int idx[KK];
     HT hv[KK];
     float2 dg;
-    df_row_ops<CH, KK>(H, i, idx, hv, dg);
+    df_row_ops<CH, KK, UH>(H, i, idx, hv, dg);
 #pragma unroll
     for (int q = 0; q < NSET; ++q) {
       float4 nb[KK];
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(256) k_evolve_df(DfEll<CH> H, const int4* __re
         const float4 own = df_load<true>(A.psi[q], e);
 #pragma unroll
         for (int k = 0; k < KK; ++k) nb[k] = df_load<true>(A.psi[q], (size_t)idx[k]);
-        const float4 y = df_step<CH, KK, true>(hv, dg, own, nb, make_float4(0.f, 0.f, 0.f, 0.f));
+        const float4 y = df_step_any<CH, KK, true, UH>(H, hv, dg, own, nb, make_float4(0.f, 0.f, 0.f, 0.f));
         A.out[q][e] = y;
         A.t0[q][e] = own;
         DfC a = dfc_zero();
@@ -436,7 +453,7 @@ __global__ void __launch_bounds__(256) k_evolve_df(DfEll<CH> H, const int4* __re
         const float4 own = __ldg(A.t1[q] + e);
 #pragma unroll
         for (int k = 0; k < KK; ++k) nb[k] = __ldg(A.t1[q] + idx[k]);
-        const float4 y = df_step<CH, KK, false>(hv, dg, own, nb, A.t2[q][e]);
+        const float4 y = df_step_any<CH, KK, false, UH>(H, hv, dg, own, nb, A.t2[q][e]);
         DfC a = dfc_of(A.acc[q][e]);
         dfc_mac(a, c0, y);
         const float4 f = dfc_out(a, false);
@@ -483,7 +500,7 @@ struct DfMsd {
   float4* accx;
 };
 
-template <bool CH, int KK, int PH>
+template <bool CH, int KK, int PH, bool UH = false>
 __global__ void __launch_bounds__(256) k_msd_evolve_df(DfEll<CH> H, const int4* __restrict__ tab, DfMsd B, float4 c0,
                                                        float4 c1, double2* __restrict__ partial, int nblocks,
                                                        int slot) {
@@ -504,7 +521,7 @@ __global__ void __launch_bounds__(256) k_msd_evolve_df(DfEll<CH> H, const int4* 
     int idx[KK];
     HT hv[KK];
     float2 dg;
-    df_row_ops<CH, KK>(H, i, idx, hv, dg);
+    df_row_ops<CH, KK, UH>(H, i, idx, hv, dg);
     float4 uo, zo;  // u_m and z_m at this element
     float4 u_own, z_own;
     if (PH == 0) {
@@ -513,14 +530,20 @@ __global__ void __launch_bounds__(256) k_msd_evolve_df(DfEll<CH> H, const int4* 
       float4 un[KK];
 #pragma unroll
       for (int k = 0; k < KK; ++k) un[k] = df_load<true>(B.p, (size_t)idx[k]);
-      uo = df_step<CH, KK, true>(hv, dg, u_own, un, make_float4(0.f, 0.f, 0.f, 0.f));
+      uo = df_step_any<CH, KK, true, UH>(H, hv, dg, u_own, un, make_float4(0.f, 0.f, 0.f, 0.f));
       DfC a = dfc_zero();
       dfc_mac(a, dg, z_own);
+      float4 zn[KK];
 #pragma unroll
-      for (int k = 0; k < KK; ++k) {
-        dfc_mac(a, hv[k], df_load<true>(B.px, (size_t)idx[k]));
-        dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
+      for (int k = 0; k < KK; ++k) zn[k] = df_load<true>(B.px, (size_t)idx[k]);
+      if constexpr (UH) {
+        dfc_mac_sum<KK>(a, H.h0, zn);
+      } else {
+#pragma unroll
+        for (int k = 0; k < KK; ++k) dfc_mac(a, hv[k], zn[k]);
       }
+#pragma unroll
+      for (int k = 0; k < KK; ++k) dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
       zo = dfc_out(a, true);
     } else {
       u_own = __ldg(B.u1 + e);
@@ -528,14 +551,20 @@ __global__ void __launch_bounds__(256) k_msd_evolve_df(DfEll<CH> H, const int4* 
       float4 un[KK];
 #pragma unroll
       for (int k = 0; k < KK; ++k) un[k] = __ldg(B.u1 + idx[k]);
-      uo = df_step<CH, KK, false>(hv, dg, u_own, un, B.u2[e]);
+      uo = df_step_any<CH, KK, false, UH>(H, hv, dg, u_own, un, B.u2[e]);
       DfC a = dfc_neg(B.z2[e]);
       dfc_mac(a, dg, z_own);
+      float4 zn[KK];
 #pragma unroll
-      for (int k = 0; k < KK; ++k) {
-        dfc_mac(a, hv[k], __ldg(B.z1 + idx[k]));
-        dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
+      for (int k = 0; k < KK; ++k) zn[k] = __ldg(B.z1 + idx[k]);
+      if constexpr (UH) {
+        dfc_mac_sum<KK>(a, H.h0, zn);
+      } else {
+#pragma unroll
+        for (int k = 0; k < KK; ++k) dfc_mac(a, hv[k], zn[k]);
       }
+#pragma unroll
+      for (int k = 0; k < KK; ++k) dfc_mac(a, __ldg(H.xhop + (size_t)k * H.n + i), un[k]);
       zo = dfc_out(a, false);
     }
     if (PH == 0) {

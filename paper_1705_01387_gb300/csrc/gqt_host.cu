@@ -1336,28 +1336,37 @@ static void launch_evolve_df(gqt_ham* h, void* const* psi, const std::vector<dou
         A.acc[q] = ACC[q];
       }
       const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-      k_evolve_df<CH, KK, NSET, 0><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[0]),
-                                                                 Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
-      check_launch("k_evolve_df(0)");
-      if (Np <= 2) {
-        k_evolve_df<CH, KK, NSET, 3><<<nb, h->threads, smem, s2>>>(H, tab, A, zero, zero, partial, nb, NSET);
-        check_launch("k_evolve_df(3)");
-        return;
-      }
-      for (int m = 2; m < Np; ++m) {
-        for (int q = 0; q < NSET; ++q) {
-          A.t1[q] = (m - 1) % 2 == 1 ? W1[q] : W2[q];
-          A.out[q] = (m % 2 == 1) ? W1[q] : W2[q];
-          A.t2[q] = A.out[q];
+      auto orders = [&](auto uh) {
+        constexpr bool UH = decltype(uh)::value && !CH;  // one common hopping: no hop array read
+        k_evolve_df<CH, KK, NSET, 0, UH><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[0]),
+                                                                       Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
+        check_launch("k_evolve_df(0)");
+        if (Np <= 2) {
+          k_evolve_df<CH, KK, NSET, 3, UH><<<nb, h->threads, smem, s2>>>(H, tab, A, zero, zero, partial, nb, NSET);
+          check_launch("k_evolve_df(3)");
+          return;
         }
-        size_t pe = prof_begin(s2);
-        if (m == Np - 1)
-          k_evolve_df<CH, KK, NSET, 2><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb, NSET);
-        else
-          k_evolve_df<CH, KK, NSET, 1><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb, NSET);
-        check_launch("k_evolve_df");
-        prof_end(pe, 1 + NSET, s2);
-      }
+        for (int m = 2; m < Np; ++m) {
+          for (int q = 0; q < NSET; ++q) {
+            A.t1[q] = (m - 1) % 2 == 1 ? W1[q] : W2[q];
+            A.out[q] = (m % 2 == 1) ? W1[q] : W2[q];
+            A.t2[q] = A.out[q];
+          }
+          size_t pe = prof_begin(s2);
+          if (m == Np - 1)
+            k_evolve_df<CH, KK, NSET, 2, UH><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb,
+                                                                           NSET);
+          else
+            k_evolve_df<CH, KK, NSET, 1, UH><<<nb, h->threads, smem, s2>>>(H, tab, A, coef_df(c[m]), zero, partial, nb,
+                                                                           NSET);
+          check_launch("k_evolve_df");
+          prof_end(pe, 1 + NSET, s2);
+        }
+      };
+      if (h->hop_uniform)
+        orders(std::true_type());
+      else
+        orders(std::false_type());
     });
     k_norm_check<<<1, 256, 0, s2>>>(partial, NSET, nb, 1, (const int*)T.d_seg_blk.p, h->nseg, 1e-10, d_norms,
                                     (int*)h->d_flag.p);
@@ -1405,29 +1414,38 @@ static void launch_msd_df(gqt_ham* h, void* p, void* px, const std::vector<doubl
       B.accp = AP;
       B.accx = AX;
       const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-      k_msd_evolve_df<CH, KK, 0><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[0]),
-                                                               Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
-      check_launch("k_msd_evolve_df(0)");
-      if (Np <= 2) {
-        k_msd_evolve_df<CH, KK, 3><<<nb, h->threads, smem, s2>>>(H, tab, B, zero, zero, partial, nb, 2);
-        check_launch("k_msd_evolve_df(3)");
-        return;
-      }
-      for (int m = 2; m < Np; ++m) {
-        B.u1 = (m - 1) % 2 == 1 ? U1 : U2;
-        B.z1 = (m - 1) % 2 == 1 ? Z1 : Z2;
-        B.uo = (m % 2 == 1) ? U1 : U2;
-        B.zo = (m % 2 == 1) ? Z1 : Z2;
-        B.u2 = B.uo;
-        B.z2 = B.zo;
-        size_t pe = prof_begin(s2);
-        if (m == Np - 1)
-          k_msd_evolve_df<CH, KK, 2><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb, 2);
-        else
-          k_msd_evolve_df<CH, KK, 1><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb, 2);
-        check_launch("k_msd_evolve_df");
-        prof_end(pe, 4, s2);
-      }
+      auto orders = [&](auto uh) {
+        constexpr bool UH = decltype(uh)::value && !CH;  // one common hopping: no hop array read
+        k_msd_evolve_df<CH, KK, 0, UH><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[0]),
+                                                                     Np > 1 ? coef_df(c[1]) : zero, partial, nb, 0);
+        check_launch("k_msd_evolve_df(0)");
+        if (Np <= 2) {
+          k_msd_evolve_df<CH, KK, 3, UH><<<nb, h->threads, smem, s2>>>(H, tab, B, zero, zero, partial, nb, 2);
+          check_launch("k_msd_evolve_df(3)");
+          return;
+        }
+        for (int m = 2; m < Np; ++m) {
+          B.u1 = (m - 1) % 2 == 1 ? U1 : U2;
+          B.z1 = (m - 1) % 2 == 1 ? Z1 : Z2;
+          B.uo = (m % 2 == 1) ? U1 : U2;
+          B.zo = (m % 2 == 1) ? Z1 : Z2;
+          B.u2 = B.uo;
+          B.z2 = B.zo;
+          size_t pe = prof_begin(s2);
+          if (m == Np - 1)
+            k_msd_evolve_df<CH, KK, 2, UH><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb,
+                                                                         2);
+          else
+            k_msd_evolve_df<CH, KK, 1, UH><<<nb, h->threads, smem, s2>>>(H, tab, B, coef_df(c[m]), zero, partial, nb,
+                                                                         2);
+          check_launch("k_msd_evolve_df");
+          prof_end(pe, 4, s2);
+        }
+      };
+      if (h->hop_uniform)
+        orders(std::true_type());
+      else
+        orders(std::false_type());
     });
     k_norm_check_msd<<<1, 256, 0, s2>>>(partial, nb, 1, (const int*)T.d_seg_blk.p, h->nseg, 1e-10,
                                         (int*)h->d_flag.p);

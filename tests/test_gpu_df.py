@@ -38,6 +38,10 @@ MODELS = {
     "square41x29": lambda: (S.square(41, 29, -1.0, 4.0, seed=5), S.energy_scale_rule(4, -1.0, 4.0)),
     "cubic13": lambda: (S.cubic(13, -1.0, 16.5, seed=7), S.energy_scale_rule(6, -1.0, 16.5)),
     "chain5001": lambda: (S.chain(5001, -1.0, 4.0, seed=9), S.energy_scale_rule(2, -1.0, 4.0)),
+    # real hoppings that are not all equal (bonds to vacancies are zero): the
+    # general form, where the others take the one-common-hopping form
+    "honeycomb37x23_vac": lambda: (S.honeycomb(37, 23, -2.7, 2.0, seed=4, vacancy_frac=0.02),
+                                   S.energy_scale_rule(3, -2.7, 2.0)),
 }
 
 
